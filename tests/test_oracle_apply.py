@@ -1,0 +1,93 @@
+"""Pins of the oracle's matrix-free apply and CG."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import apply as ap
+from oracle import stencil as st
+from oracle.cg import cg
+
+
+def _asym2d():
+    return st.outer_product(st.d1_forward(), st.d2_forward())
+
+
+def test_apply_equals_dense_matrix_periodic_and_zero():
+    """Brute force with one-sided stencils, so a sign or axis mix-up fails."""
+    rng = np.random.default_rng(1)
+    for s, shape in [(_asym2d(), (6, 7)),
+                     (st.outer_product(st.outer_product(st.d1_forward(), st.d1_central2()), st.d2_forward()), (5, 4, 6)),
+                     (st.bilaplacian(2, 4), (9, 11))]:
+        w = {k: float(v) for k, v in s.coeffs}
+        x = rng.uniform(-1, 1, shape)
+        for bc in ["periodic", "zero"]:
+            M = ap.dense_matrix(w, shape, bc).astype(np.float64)
+            y = ap.apply(w, x, bc)
+            assert np.allclose(y.ravel(), M @ x.ravel(), rtol=1e-13, atol=1e-13)
+
+
+def test_ghosted_matches_periodic_padding():
+    rng = np.random.default_rng(2)
+    s = st.bilaplacian(3, 4)
+    w = {k: float(v) for k, v in s.coeffs}
+    x = rng.uniform(-1, 1, (12, 10, 9))
+    R = 4
+    xp = np.pad(x, R, mode="wrap")
+    assert np.array_equal(ap.apply(w, xp, "ghosted", R), ap.apply(w, x, "periodic"))
+
+
+@pytest.mark.parametrize("ndim,order,n", [(2, 2, 32), (2, 4, 24), (3, 2, 12), (3, 4, 16)])
+def test_fourier_modes_are_eigenvectors(ndim, order, n):
+    """On a periodic grid every DFT mode is an eigenvector of Lap o Lap with
+    eigenvalue (sum_a lambda(theta_a))^2, lambda the 1D symbol
+    (2 - 2cos t)/h^2 or (30 - 32 cos t + 2 cos 2t)/(12 h^2)."""
+    h = 1.0 / n
+    B = st.bilaplacian(ndim, order)
+    w = st.fp_weights(B, Fraction(1, n), np.float64)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        ks = rng.integers(0, n, ndim)
+        grids = np.meshgrid(*[np.arange(n)] * ndim, indexing="ij")  # array axes (z,)y,x
+        phase = sum(2 * np.pi * k * g / n for k, g in zip(ks, grids))
+        v = np.cos(phase)
+        lam = 0.0
+        for k in ks:
+            t = 2 * np.pi * k / n
+            lam += (2 - 2 * np.cos(t)) / h**2 if order == 2 else (30 - 32 * np.cos(t) + 2 * np.cos(2 * t)) / (12 * h**2)
+        sigma = lam * lam
+        y = ap.apply(w, v, "periodic")
+        scale = sum(abs(x) for x in w.values())
+        assert np.max(np.abs(y - sigma * v)) <= 64 * np.finfo(float).eps * scale
+
+
+def test_checkerboard_is_the_largest_mode():
+    """Checkerboard on an even grid: eigenvalue sum|w| h^-4 (64/h^4 for the
+    13-point operator)."""
+    n = 16
+    B = st.bilaplacian(2, 2)
+    w = st.fp_weights(B, Fraction(1, n), np.float64)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    v = (-1.0) ** (x + y)
+    assert np.array_equal(ap.apply(w, v, "periodic"), 64.0 * n**4 * v)
+
+
+def test_cg_matches_direct_solve():
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(40, 40))
+    A = A @ A.T + 40 * np.eye(40)
+    b = rng.normal(size=40)
+    x, it, res, ok = cg(lambda v: A @ v, b, None, 1e-12)
+    assert ok and res <= 1e-11
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+    # exact arithmetic would finish in at most n steps; a well-conditioned
+    # 40x40 system stays close to that
+    assert it <= 80
+
+
+def test_cg_zero_rhs_and_x0():
+    x, it, res, ok = cg(lambda v: 2 * v, np.zeros(5))
+    assert ok and it == 0 and np.all(x == 0)
+    b = np.arange(1.0, 6.0)
+    x, it, res, ok = cg(lambda v: 2 * v, b, b / 2)
+    assert ok and it == 0 and np.allclose(x, b / 2)
