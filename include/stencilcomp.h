@@ -1,0 +1,157 @@
+/*
+ * stencilcomp.h -- C ABI of the GB300 (sm_103a) stencil-composition library.
+ *
+ * Method: Mishra, Salac & Knepley, "On the order of accuracy for finite
+ * difference approximations of partial differential equations using stencil
+ * composition" (arXiv 2205.03354).  Stencils are composed exactly (Sec. 2.2,
+ * Eq. C=B(A)); the composed wide stencil is applied matrix-free on 2D/3D
+ * structured grids, inside conjugate-gradient solves of the biharmonic plate
+ * problem (Sec. 3.3) and of semi-implicit Cahn-Hilliard steps (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - All functions return an sc_status (0 = SC_OK).  sc_last_error() gives a
+ *    short human-readable reason for the last failure on the calling thread.
+ *  - The caller owns every buffer it passes; the library never frees caller
+ *    memory.  "_dev" pointers are CUDA device pointers on the current device,
+ *    "_host" pointers are host memory (pinned memory gives faster copies).
+ *  - Grids are dense row-major arrays with x fastest: a 3D grid of dims
+ *    {nx, ny, nz} is indexed [z][y][x], a 2D grid [y][x].  An offset vector is
+ *    written (dx, dy, dz).
+ *  - "stream" is a cudaStream_t (0 = legacy default stream).  Device work is
+ *    enqueued on it; functions that must read results back (solves) block
+ *    until their work on that stream has finished.
+ *  - The library never calls cudaMalloc on a user path: every device buffer,
+ *    including scratch ("work") space, is passed in by the caller, whose size
+ *    is given by the matching *_work_bytes query.  The serving loop
+ *    sub-allocates from a caller-provided device arena.
+ *  - Invalid arguments return SC_EINVAL before any device work is enqueued.
+ *
+ * The Python binding (paper_2205_03354_gb300) exposes each function under
+ * the same name without the "sc_" prefix.
+ */
+#ifndef STENCILCOMP_H
+#define STENCILCOMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sc_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  SC_OK = 0,
+  SC_EINVAL = 1,      /* bad argument (size, pointer, alignment, mode)       */
+  SC_ENOMEM = 2,      /* caller-provided work/arena space too small          */
+  SC_ENOTCONV = 3,    /* iteration cap reached before the tolerance          */
+  SC_EBREAKDOWN = 4,  /* CG breakdown: p^T A p <= 0 or a non-finite scalar    */
+  SC_ETIMEOUT = 5,    /* a bounded device wait gave up (never expected)       */
+  SC_EBUSY = 6,       /* server: no admission possible right now              */
+  SC_ECUDA = 7,       /* a CUDA runtime call failed                           */
+  SC_EOVERFLOW = 8,   /* exact integer arithmetic would overflow              */
+  SC_EPENDING = 9     /* server: request still in flight                      */
+} sc_status;
+
+typedef enum { SC_F64 = 0, SC_F32 = 1 } sc_dtype;
+
+/* Boundary handling of an apply:
+ *  SC_BC_PERIODIC: x and y have dims n; indices wrap around.
+ *  SC_BC_GHOSTED:  x has dims n + 2R (an R-wide ghost ring, R = stencil
+ *                  radius), y has dims n (the interior).
+ *  SC_BC_ZERO:     x and y have dims n; values outside the grid are zero. */
+typedef enum { SC_BC_PERIODIC = 0, SC_BC_GHOSTED = 1, SC_BC_ZERO = 2 } sc_bc;
+
+/* 1D stencils printed in the paper (a_i = num_i / den * h^-hpow). */
+typedef enum {
+  SC_D1_C2 = 0,  /* (f_1 - f_-1)/(2h),           Sec. 2.1.1, Eq. f'stencil      */
+  SC_D2_C2 = 1,  /* [1,-2,1]/h^2,                Sec. 2.1.2                    */
+  SC_D1_C4 = 2,  /* (8f_1 - f_2 + f_-2 - 8f_-1)/(12h), Sec. 2.2.3, Eq. 4orderf' */
+  SC_D2_C4 = 3,  /* [-1,16,-30,16,-1]/(12h^2),   the fourth-order 2nd derivative
+                    composed in Sec. 3.2                                       */
+  SC_D1_FWD = 4, /* (f_1 - f_0)/h,               Sec. 2.2.1                    */
+  SC_D2_FWD = 5  /* (f_2 - 2f_1 + f_0)/h^2,      Sec. 2.2.1                    */
+} sc_kind1d;
+
+#define SC_MAX_NDIM 3
+#define SC_MAX_PTS 2197 /* 13^3: every 3D stencil of radius <= 6 */
+#define SC_MAX_APPLY_RADIUS 4
+
+/* An exact stencil (Def. 2.1): weight at offset off[i] is
+ * num[i] / den * h^-hpow.  Offsets unused beyond ndim are 0.  Points are kept
+ * sorted lexicographically by (dx, dy, dz) with no zero weights, and den > 0
+ * with gcd(den, num...) = 1.  Plain value type: no library-owned memory. */
+typedef struct {
+  int32_t ndim;
+  int32_t npts;
+  int32_t hpow;
+  int32_t radius; /* max |offset component| */
+  int64_t den;
+  int32_t off[SC_MAX_PTS][SC_MAX_NDIM];
+  int64_t num[SC_MAX_PTS];
+} sc_stencil;
+
+/* Library version, e.g. 100 for 1.0.0. */
+int32_t sc_version(void);
+/* Reason for the last non-OK status returned on this thread ("" if none). */
+const char *sc_last_error(void);
+
+/* ---- Exact stencil algebra (host only, no device work) ------------------ */
+
+/* One of the 1D stencils above (ndim = 1). */
+int sc_stencil_1d(int32_t kind, sc_stencil *out);
+
+/* A 1D stencil acting along `axis` (0 = x) of an ndim-dimensional lattice,
+ * the identity on the other axes (Sec. 2.3). */
+int sc_stencil_embed(const sc_stencil *s1d, int32_t ndim, int32_t axis, sc_stencil *out);
+
+/* a + b for stencils of equal ndim and hpow (the Taylor series of source
+ * points form a vector space, Sec. 2.1).  SC_EOVERFLOW on int64 overflow. */
+int sc_stencil_add(const sc_stencil *a, const sc_stencil *b, sc_stencil *out);
+
+/* Sum over axes of the 1D second-derivative stencil of `order` (2 or 4):
+ * the Laplacian the paper composes with itself (Sec. 3.3). */
+int sc_laplacian(int32_t ndim, int32_t order, sc_stencil *out);
+
+/* Stencil composition C = B(A), B = outer, A = inner (Sec. 2.2, Eq. C=B(A)):
+ * offsets add, weights multiply, c_k = sum_{u_i+v_j=k} a_i b_j, and the
+ * h-powers add.  Exact in int64; SC_EOVERFLOW if any intermediate would
+ * overflow, SC_EINVAL if the result exceeds SC_MAX_PTS points or the
+ * dimensions differ.  Composition is only meaningful when the same inner
+ * stencil is used at every outer point (Sec. 5, closing caveat), which holds
+ * by construction here.  `out` may alias neither input. */
+int sc_compose_stencil(const sc_stencil *outer, const sc_stencil *inner, sc_stencil *out);
+
+/* Floating-point weights of s for lattice spacing h = h_num / h_den
+ * (h_num, h_den > 0): each weight is the exact rational num_i/den *
+ * (h_den/h_num)^hpow rounded ONCE to the nearest double (dtype SC_F64) or
+ * float (SC_F32), ties to even.  host_out receives npts values in the order
+ * of s->off.  SC_EOVERFLOW if the exact value needs more than 127 bits. */
+int sc_stencil_weights(const sc_stencil *s, int64_t h_num, int64_t h_den, int32_t dtype,
+                       void *host_out);
+
+/* ---- Matrix-free apply (device) ------------------------------------------ */
+
+/* y = A x with the composed stencil s (flat evaluation, y_i = sum_k w_k
+ * x_{i+k}, weights from sc_stencil_weights with h = h_num/h_den), on a grid
+ * of interior dims {nx, ny[, nz]} = dims[0..ndim-1].  s->ndim must be 2 or 3
+ * and s->radius <= SC_MAX_APPLY_RADIUS.  x and y are device arrays of `dtype`
+ * (layout per `bc` above) and must not overlap.  Asynchronous on `stream`. */
+int sc_apply_composed(const sc_stencil *s, int32_t dtype, int32_t bc, const int64_t *dims,
+                      int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                      sc_stream_t stream);
+
+/* Same as sc_apply_composed, with x and y in HOST memory: copies x to the
+ * device work space, applies, copies y back and waits for the stream.
+ * work_bytes >= sc_apply_host_work_bytes(...). */
+size_t sc_apply_host_work_bytes(const sc_stencil *s, int32_t dtype, int32_t bc,
+                                const int64_t *dims);
+int sc_apply_composed_host(const sc_stencil *s, int32_t dtype, int32_t bc, const int64_t *dims,
+                           int64_t h_num, int64_t h_den, const void *x_host, void *y_host,
+                           void *work_dev, size_t work_bytes, sc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STENCILCOMP_H */

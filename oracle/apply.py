@@ -86,3 +86,36 @@ def dense_matrix(coeffs: dict, shape: tuple, bc: str) -> np.ndarray:
     if ndim == 0:
         raise ValueError("empty shape")
     return M
+
+
+def apply_at(weights: dict, x: np.ndarray, bc: str, points: np.ndarray, radius: int | None = None) -> np.ndarray:
+    """The same sum evaluated only at the listed output points (rows of array
+    indices in array-axis order), one point at a time: lets a full-size
+    device result be checked on a sample."""
+    x = np.asarray(x)
+    offs = sorted(weights)
+    if radius is None:
+        radius = max(max(abs(v) for v in k) for k in offs)
+    R = radius
+    out = np.zeros(len(points), dtype=np.float64)
+    shape_out = tuple(s - 2 * R for s in x.shape) if bc == "ghosted" else x.shape
+    for n, p in enumerate(points):
+        acc = 0.0
+        for k in offs:
+            sh = _axis_shift(k)
+            idx = []
+            ok = True
+            for pi, s, m in zip(p, sh, shape_out):
+                q = int(pi) + s
+                if bc == "periodic":
+                    q %= m
+                elif bc == "ghosted":
+                    q += R
+                elif not (0 <= q < m):
+                    ok = False
+                    break
+                idx.append(q)
+            if ok:
+                acc += float(weights[k]) * float(x[tuple(idx)])
+        out[n] = acc
+    return out

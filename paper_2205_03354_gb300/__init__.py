@@ -1,0 +1,16 @@
+"""Python binding of libstencilcomp, the GB300 (sm_103a) stencil-composition
+library (Mishra, Salac & Knepley, arXiv 2205.03354).
+
+Argument marshalling only: every function forwards to the C ABI declared in
+include/stencilcomp.h under the same name with an ``sc_`` prefix.  Device
+arrays are torch CUDA tensors (PyTorch provides device memory and streams);
+all computation runs in the library's CUDA kernels.  There is no CPU
+fallback: if the compiled library is missing, import fails loudly.
+"""
+from __future__ import annotations
+
+from ._lib_loader import lib, LIB_PATH, ScError, check  # noqa: F401
+from .stencil import (Stencil, stencil_1d, stencil_embed, stencil_add, laplacian,  # noqa: F401
+                      compose_stencil, stencil_weights, D1_C2, D2_C2, D1_C4, D2_C4, D1_FWD, D2_FWD)
+from .ops import (apply_composed, apply_composed_host, apply_host_work_bytes,  # noqa: F401
+                  F64, F32, BC_PERIODIC, BC_GHOSTED, BC_ZERO)

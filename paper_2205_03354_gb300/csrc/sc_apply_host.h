@@ -1,0 +1,31 @@
+// Host-side interface of the apply dispatch, shared by the solver and
+// serving translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/stencilcomp.h"
+
+namespace sc {
+
+struct ApplyReq {
+  const sc_stencil *s;
+  int dtype;
+  int bc;
+  const int64_t *dims;
+  int64_t h_num, h_den;
+  const void *x;
+  void *y;
+};
+
+int validate_apply(const sc_stencil *s, int dtype, int bc, const int64_t *dims, int64_t h_num,
+                   int64_t h_den);
+// Enqueues y = A x on `st` (no validation of pointers).
+int apply_enqueue(const ApplyReq &q, cudaStream_t st);
+size_t grid_elems(const sc_stencil *s, int bc, const int64_t *dims, bool input);
+int num_sms();
+// Testing/tuning knob: fixes the number of output planes per CTA (0 = auto).
+void set_apply_planes_override(int h);
+
+}  // namespace sc

@@ -1,0 +1,82 @@
+"""Device entry points taking torch tensors (marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib_loader import check, lib
+from .stencil import Stencil
+
+F64, F32 = 0, 1
+BC_PERIODIC, BC_GHOSTED, BC_ZERO = 0, 1, 2
+_BC = {"periodic": BC_PERIODIC, "ghosted": BC_GHOSTED, "zero": BC_ZERO}
+_P = ctypes.POINTER(Stencil)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+lib.sc_apply_composed.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+lib.sc_apply_composed.restype = ctypes.c_int
+lib.sc_apply_host_work_bytes.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _I64P]
+lib.sc_apply_host_work_bytes.restype = ctypes.c_size_t
+lib.sc_apply_composed_host.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+lib.sc_apply_composed_host.restype = ctypes.c_int
+
+
+def dtype_code(t) -> int:
+    if t == torch.float64:
+        return F64
+    if t == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def bc_code(bc) -> int:
+    return _BC[bc] if isinstance(bc, str) else int(bc)
+
+
+def dims_arg(dims):
+    arr = (ctypes.c_int64 * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    return arr
+
+
+def stream_arg(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def apply_composed(s: Stencil, x: torch.Tensor, y: torch.Tensor, bc="periodic", h=(1, 1),
+                   dims=None, stream=None) -> torch.Tensor:
+    """y = A x with the composed stencil s (flat evaluation) on the device.
+    ``dims`` = interior (nx, ny[, nz]); defaults to y's shape reversed."""
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous CUDA tensors")
+    if x.dtype != y.dtype:
+        raise TypeError("x and y dtypes differ")
+    if dims is None:
+        dims = tuple(reversed(y.shape))
+    check(lib.sc_apply_composed(ctypes.byref(s), dtype_code(y.dtype), bc_code(bc), dims_arg(dims),
+                                int(h[0]), int(h[1]), ctypes.c_void_p(x.data_ptr()),
+                                ctypes.c_void_p(y.data_ptr()), stream_arg(stream)))
+    return y
+
+
+def apply_host_work_bytes(s: Stencil, dtype, bc, dims) -> int:
+    return int(lib.sc_apply_host_work_bytes(ctypes.byref(s), dtype_code(dtype), bc_code(bc), dims_arg(dims)))
+
+
+def apply_composed_host(s: Stencil, x: torch.Tensor, y: torch.Tensor, work: torch.Tensor,
+                        bc="periodic", h=(1, 1), dims=None, stream=None) -> torch.Tensor:
+    """Same operator with x, y in host memory (pinned for speed); copies in
+    and out through the device work buffer ``work`` inside the call."""
+    if x.is_cuda or y.is_cuda or not work.is_cuda:
+        raise ValueError("x, y must be host tensors and work a device tensor")
+    if dims is None:
+        dims = tuple(reversed(y.shape))
+    check(lib.sc_apply_composed_host(ctypes.byref(s), dtype_code(y.dtype), bc_code(bc), dims_arg(dims),
+                                     int(h[0]), int(h[1]), ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                     work.numel() * work.element_size(), stream_arg(stream)))
+    return y

@@ -1,0 +1,159 @@
+"""GPU parity of the composed-stencil apply against the FP64 oracle.
+
+Tolerances (derived from the arithmetic):
+  * FP64: normwise ||y - y_ref||_2 <= 1e-12 ||y_ref||_2 on random fields, and
+    elementwise |y - y_ref| <= npts * eps64 * sum_k |w_k x_{i+k}|;
+  * FP32 (inputs and weights rounded to float32, accumulation in float32):
+    elementwise |y - y_ref| <= npts * eps32 * sum_k |w_k x_{i+k}|, where
+    y_ref is the exact-input FP64 oracle sum of the same float32 data.
+"""
+from fractions import Fraction
+
+import zlib
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.libutil import ensure_built  # noqa: E402
+
+ensure_built()
+import paper_2205_03354_gb300 as sc  # noqa: E402
+from oracle import apply as oap  # noqa: E402
+from oracle import stencil as ost  # noqa: E402
+from synth_inputs import fields  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def lib_bilap(ndim, order):
+    L = sc.laplacian(ndim, order)
+    return sc.compose_stencil(L, L)
+
+
+def oracle_weights(s, h, dt):
+    """Oracle's own correctly rounded weights of the oracle's own composition."""
+    return ost.fp_weights(s, h, dt)
+
+
+def check(y_gpu, x_host, w, bc, R, dt, npts):
+    y_ref = oap.apply(w, x_host.astype(np.float64), bc, R)
+    absw = {k: abs(float(v)) for k, v in w.items()}
+    mag = oap.apply(absw, np.abs(x_host.astype(np.float64)), bc, R)
+    eps = np.finfo(dt).eps
+    err = np.abs(y_gpu.astype(np.float64) - y_ref)
+    assert np.all(err <= npts * eps * mag + 1e-300), float(np.max(err / (mag + 1e-300)))
+    if dt == np.float64:
+        assert np.linalg.norm(err) <= 1e-12 * np.linalg.norm(y_ref)
+
+
+CASES = [
+    # ndim, order, interior dims (x, y[, z]) spanning several tiles + ragged tails
+    (2, 2, (1100, 301)), (2, 4, (1100, 301)), (2, 4, (1101, 97)), (2, 2, (16, 9)),
+    (3, 2, (150, 40, 37)), (3, 4, (150, 40, 37)), (3, 4, (67, 19, 23)), (3, 2, (8, 8, 8)),
+]
+
+
+@pytest.mark.parametrize("ndim,order,dims", CASES)
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("bc", ["periodic", "zero", "ghosted"])
+def test_apply_matches_oracle(ndim, order, dims, dt, bc):
+    os_ = ost.bilaplacian(ndim, order)
+    R = os_.radius
+    n = dims[0]
+    h = Fraction(1, n)
+    w = oracle_weights(os_, h, dt)
+    shape = tuple(reversed(dims))
+    xshape = tuple(s + 2 * R for s in shape) if bc == "ghosted" else shape
+    x = fields.uniform(xshape, seed=zlib.crc32(repr((ndim, order, dims, bc)).encode()), dtype=dt)
+    s = lib_bilap(ndim, order)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.full(shape, float("nan"), dtype=xt.dtype, device=DEV)
+    sc.apply_composed(s, xt, yt, bc=bc, h=(1, n), dims=dims)
+    torch.cuda.synchronize()
+    check(yt.cpu().numpy(), x, w, bc, R, dt, os_.npts)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_other_supports(dt):
+    """Stencils outside the Lap o Lap class go through the box kernels:
+    a one-sided mixed derivative (2D, radius 2) and a 3D box of radius 1."""
+    rng = np.random.default_rng(5)
+    cases = [
+        (sc.compose_stencil(sc.stencil_embed(sc.stencil_1d(sc.D2_FWD), 2, 0),
+                            sc.stencil_embed(sc.stencil_1d(sc.D1_C2), 2, 1)),
+         ost.outer_product(ost.d2_forward(), ost.d1_central2()), (300, 50)),
+        (sc.compose_stencil(sc.compose_stencil(sc.stencil_embed(sc.stencil_1d(sc.D1_C2), 3, 0),
+                                               sc.stencil_embed(sc.stencil_1d(sc.D1_FWD), 3, 1)),
+                            sc.stencil_embed(sc.stencil_1d(sc.D1_C2), 3, 2)),
+         ost.outer_product(ost.outer_product(ost.d1_central2(), ost.d1_forward()), ost.d1_central2()),
+         (70, 20, 11)),
+    ]
+    for s, os_, dims in cases:
+        assert s.points() == {k: v for k, v in os_.coeffs}
+        w = oracle_weights(os_, Fraction(1, 8), dt)
+        shape = tuple(reversed(dims))
+        x = rng.uniform(-1, 1, shape).astype(dt)
+        for bc in ["periodic", "zero"]:
+            yt = torch.empty(shape, dtype=torch.float64 if dt == np.float64 else torch.float32, device=DEV)
+            sc.apply_composed(s, torch.from_numpy(x).to(DEV), yt, bc=bc, h=(1, 8), dims=dims)
+            torch.cuda.synchronize()
+            check(yt.cpu().numpy(), x, w, bc, os_.radius, dt, os_.npts)
+
+
+def test_host_buffer_entry_point_matches_device_one():
+    s = lib_bilap(2, 4)
+    x = torch.from_numpy(fields.uniform((257, 520), seed=9)).pin_memory()
+    y = torch.empty_like(x).pin_memory()
+    work = torch.empty(sc.apply_host_work_bytes(s, torch.float64, "periodic", (520, 257)),
+                       dtype=torch.uint8, device=DEV)
+    sc.apply_composed_host(s, x, y, work, bc="periodic", h=(1, 520))
+    yd = torch.empty((257, 520), dtype=torch.float64, device=DEV)
+    sc.apply_composed(s, x.to(DEV), yd, bc="periodic", h=(1, 520))
+    torch.cuda.synchronize()
+    assert torch.equal(yd.cpu(), y)
+
+
+@pytest.mark.parametrize("ndim,n,dt", [(2, 8192, np.float32), (2, 8192, np.float64),
+                                       (3, 512, np.float32), (3, 512, np.float64)])
+def test_full_size_sampled(ndim, n, dt):
+    """The apply-sweep sizes in the launch configuration the bench times,
+    checked on 400 sampled points (incl. edges and corners) against the
+    oracle evaluated point by point."""
+    shape = (n,) * ndim
+    x = fields.uniform(shape, seed=1234 + ndim, dtype=dt)
+    s = lib_bilap(ndim, 4)
+    os_ = ost.bilaplacian(ndim, 4)
+    w = oracle_weights(os_, Fraction(1, n), dt)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.empty_like(xt)
+    sc.apply_composed(s, xt, yt, bc="periodic", h=(1, n))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(77)
+    pts = rng.integers(0, n, size=(400, ndim))
+    pts[:8] = [[0] * ndim, [n - 1] * ndim, [0, n - 1] + [0] * (ndim - 2), [n - 1, 0] + [n - 1] * (ndim - 2),
+               [1] * ndim, [n - 2] * ndim, [3] * ndim, [n - 4] * ndim]
+    y = yt.cpu().numpy()
+    got = np.array([y[tuple(p)] for p in pts], dtype=np.float64)
+    ref = oap.apply_at(w, x, "periodic", pts, os_.radius)
+    absw = {k: abs(float(v)) for k, v in w.items()}
+    mag = oap.apply_at(absw, np.abs(x), "periodic", pts, os_.radius)
+    eps = np.finfo(dt).eps
+    assert np.all(np.abs(got - ref) <= os_.npts * eps * mag)
+
+
+def test_invalid_arguments_are_rejected():
+    s = lib_bilap(2, 2)
+    x = torch.zeros((8, 8), dtype=torch.float64, device=DEV)
+    with pytest.raises(sc.ScError):
+        sc.apply_composed(s, x, x, bc="periodic", h=(1, 8))  # aliasing
+    y = torch.zeros((8, 8), dtype=torch.float64, device=DEV)
+    with pytest.raises(sc.ScError):
+        sc.apply_composed(s, x, y, bc="periodic", h=(1, 8), dims=(0, 8))
+    with pytest.raises(sc.ScError):
+        sc.apply_composed(s, x, y, bc="periodic", h=(1, 8), dims=(3, 8))
+    s1 = sc.stencil_1d(sc.D2_C2)
+    with pytest.raises(sc.ScError):
+        sc.apply_composed(s1, x, y, bc="periodic", h=(1, 8))

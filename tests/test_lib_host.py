@@ -1,0 +1,89 @@
+"""The C-ABI library without a GPU: it loads, exports every function the
+headers declare, and its exact host algebra matches the oracle bit for bit."""
+import ctypes
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from tests.libutil import ensure_built, header_functions
+
+ensure_built()
+import paper_2205_03354_gb300 as sc  # noqa: E402
+from oracle import stencil as ost  # noqa: E402
+
+KIND = {"d1_c2": sc.D1_C2, "d2_c2": sc.D2_C2, "d1_c4": sc.D1_C4, "d2_c4": sc.D2_C4,
+        "d1_fwd": sc.D1_FWD, "d2_fwd": sc.D2_FWD}
+
+
+def test_every_declared_symbol_is_exported():
+    names = header_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(sc.lib, n)]
+    assert not missing, missing
+
+
+def _same(lib_s, orc_s):
+    assert lib_s.hpow == orc_s.hpow
+    assert lib_s.points() == {k: v for k, v in orc_s.coeffs}
+
+
+def test_1d_stencils_and_compositions_match_oracle():
+    for a, ka in KIND.items():
+        _same(sc.stencil_1d(ka), ost.STENCIL_1D[a]())
+        for b, kb in KIND.items():
+            _same(sc.compose_stencil(sc.stencil_1d(ka), sc.stencil_1d(kb)),
+                  ost.compose(ost.STENCIL_1D[a](), ost.STENCIL_1D[b]()))
+
+
+@pytest.mark.parametrize("ndim,order", [(2, 2), (3, 2), (2, 4), (3, 4), (1, 2), (1, 4)])
+def test_laplacian_and_bilaplacian_match_oracle(ndim, order):
+    L = sc.laplacian(ndim, order)
+    _same(L, ost.laplacian(ndim, order))
+    _same(sc.compose_stencil(L, L), ost.bilaplacian(ndim, order))
+    # triple composition (radius 6 in 3D at 2nd order) still exact
+    if order == 2:
+        _same(sc.compose_stencil(L, sc.compose_stencil(L, L)),
+              ost.compose(ost.laplacian(ndim, 2), ost.bilaplacian(ndim, 2)))
+
+
+def test_mixed_axis_composition_matches_oracle():
+    x = sc.stencil_embed(sc.stencil_1d(sc.D1_FWD), 2, 0)
+    y = sc.stencil_embed(sc.stencil_1d(sc.D2_C4), 2, 1)
+    _same(sc.compose_stencil(x, y), ost.outer_product(ost.d1_forward(), ost.d2_central4()))
+    _same(sc.stencil_add(sc.stencil_embed(sc.stencil_1d(sc.D2_C4), 2, 0), y), ost.laplacian(2, 4))
+
+
+@pytest.mark.parametrize("ndim,order", [(2, 2), (3, 2), (2, 4), (3, 4)])
+def test_weights_bit_exact(ndim, order):
+    L = sc.laplacian(ndim, order)
+    B = sc.compose_stencil(L, L)
+    ob = ost.bilaplacian(ndim, order)
+    keys = [k for k, _ in ob.coeffs]
+    for (hn, hd) in [(1, 64), (1, 65), (1, 8192), (1, 512), (1, 1024), (1, 2049), (8, 1), (1, 2), (3, 7)]:
+        h = Fraction(hn, hd)
+        for dt in (np.float64, np.float32):
+            w = sc.stencil_weights(B, hn, hd, dt)
+            ow = ost.fp_weights(ob, h, dt)
+            want = np.array([ow[k] for k in keys], dtype=dt)
+            assert np.array_equal(w.view(np.uint64 if dt == np.float64 else np.uint32),
+                                  want.view(np.uint64 if dt == np.float64 else np.uint32)), (hn, hd, dt)
+
+
+def test_errors_are_reported():
+    a = sc.laplacian(2, 2)
+    b = sc.laplacian(3, 2)
+    with pytest.raises(sc.ScError) as e:
+        sc.compose_stencil(a, b)
+    assert e.value.status == 1
+    big = sc.Stencil()
+    big.ndim, big.npts, big.hpow, big.radius, big.den = 1, 1, 0, 0, 1
+    big.off[0][0] = 0
+    big.num[0] = 2 ** 62
+    with pytest.raises(sc.ScError) as e:
+        sc.compose_stencil(big, big)
+    assert e.value.status == 8  # SC_EOVERFLOW
+    with pytest.raises(sc.ScError):
+        sc.laplacian(4, 2)
+    with pytest.raises(sc.ScError):
+        sc.stencil_weights(a, 0, 1)
