@@ -151,6 +151,106 @@ int sc_apply_composed_host(const sc_stencil *s, int32_t dtype, int32_t bc, const
                            int64_t h_num, int64_t h_den, const void *x_host, void *y_host,
                            void *work_dev, size_t work_bytes, sc_stream_t stream);
 
+
+/* ---- Solvers (device) ------------------------------------------------------ */
+
+typedef enum {
+  SC_PREC_F64 = 0,   /* FP64 CG throughout                                     */
+  SC_PREC_MIXED = 1, /* FP32 stencil applies and vector updates with FP32
+                        accumulation; FP64 solution, right-hand side and true
+                        residual refreshed by reliable updates                 */
+  SC_PREC_AUTO = 2   /* MIXED when the closed-form condition number estimate
+                        kappa satisfies kappa * 2^-24 <= 1e-2, else F64        */
+} sc_prec;
+
+typedef enum {
+  SC_SOLVER_PERSISTENT = 0, /* one cooperative launch runs the whole CG loop  */
+  SC_SOLVER_PLAIN = 1       /* one kernel per CG operation, host-driven loop  */
+} sc_solver_kind;
+
+typedef struct {
+  int64_t iters;   /* inner CG iterations                                      */
+  int64_t outer;   /* FP64 residual refreshes (mixed precision)                */
+  double rel_res;  /* final TRUE relative residual ||b - A x||_2 / ||b||_2,
+                      recomputed in FP64 after the solve                       */
+  int32_t status;  /* SC_OK, SC_ENOTCONV, SC_EBREAKDOWN or SC_ETIMEOUT          */
+  int32_t prec;    /* precision actually used (SC_PREC_F64 / SC_PREC_MIXED)     */
+  double seconds;  /* wall time of the call                                    */
+} sc_solve_info;
+
+/* The biharmonic plate problem of Sec. 3.3: Lap(Lap u) = g on the unit square
+ * (ndim 2) or cube (ndim 3) with N = n[a] interior nodes per axis,
+ * h = 1/(N+1) (all n[a] equal), node i at x = i h.  The operator is the
+ * composed Lap o Lap of the given Laplacian order (2: 13/25 points; the
+ * persistent solver supports order 2).  Boundary data: the R-wide ghost ring
+ * (R = 2 for order 2) of ghost_dev, an (N+2R)^ndim array laid out like the
+ * interior arrays, holds the exact solution (only the ring is read); its
+ * contribution moves to the right-hand side, b = g - A(ring), and the
+ * interior system is solved by CG from x = 0 to ||b - A x|| <= rtol ||b||.
+ * f_dev: g on the interior (N^ndim doubles); x_dev: solution (N^ndim doubles,
+ * overwritten). */
+typedef struct {
+  int32_t ndim;
+  int32_t order;
+  int64_t n[3];
+  int32_t prec;   /* sc_prec */
+  int32_t solver; /* sc_solver_kind */
+  double rtol;
+  int64_t maxit;  /* cap on inner iterations (SC_ENOTCONV when reached) */
+  const double *f_dev;
+  const double *ghost_dev;
+  double *x_dev;
+} sc_bvp;
+
+/* Device work space needed by sc_solve_biharmonic / ..._batch. */
+size_t sc_bvp_work_bytes(const sc_bvp *p);
+int sc_solve_biharmonic(const sc_bvp *p, void *work_dev, size_t work_bytes, sc_solve_info *info,
+                        sc_stream_t stream);
+
+/* `count` independent plate problems of uneven sizes and dimensions solved
+ * together: one persistent launch per precision class, each problem on its
+ * own group of CTAs (the batched persistent solver).  Results are
+ * bit-identical to solving each problem alone with the same solver and
+ * precision.  infos[count] receives per-problem results. */
+size_t sc_bvp_batch_work_bytes(const sc_bvp *probs, int32_t count);
+int sc_solve_biharmonic_batch(const sc_bvp *probs, int32_t count, void *work_dev, size_t work_bytes,
+                              sc_solve_info *infos, sc_stream_t stream);
+
+/* One semi-implicit Cahn-Hilliard step (Sec. 4.1, Eq. cahn, linear fourth-
+ * order part implicit, nonlinear part explicit) on a periodic n^ndim grid of
+ * spacing h = h_num/h_den, for `batch` independent fields stored back to back:
+ *   (I + dt M kappa Lap_h o Lap_h) u_new = u + dt M Lap_h f'(u),
+ * Lap_h the Laplacian of the given order (2), f'(u) = u^3 - u (chem 0) or
+ * 2 rho (u - ca)(u - cb)(2u - ca - cb) (chem 1, the double well of Sec. 4.1).
+ * CG starts from u; after it the mean of u_new is set to that of the
+ * right-hand side (the periodic operator conserves the mean exactly, so
+ * this removes only rounding drift).  u_dev is updated in place;
+ * infos[batch] receives per-field results. */
+typedef struct {
+  int32_t ndim;
+  int32_t order;
+  int64_t n[3];
+  int32_t batch;
+  int64_t h_num, h_den;
+  double dt, M, kappa;
+  int32_t chem;
+  double rho, ca, cb;
+  int32_t prec;
+  int32_t solver;
+  double rtol;
+  int64_t maxit;
+} sc_ch;
+
+size_t sc_ch_work_bytes(const sc_ch *p);
+int sc_ch_step(const sc_ch *p, double *u_dev, void *work_dev, size_t work_bytes, sc_solve_info *infos,
+               sc_stream_t stream);
+
+/* Mass sum(u) and free energy F(u) = h^d sum[f(u) + kappa/2 sum_a (D+_a u)^2]
+ * (forward differences, periodic) of each field, written to host arrays
+ * mass[batch], energy[batch].  Deterministic reduction order. */
+int sc_ch_stats(const sc_ch *p, const double *u_dev, double *mass_host, double *energy_host,
+                void *work_dev, size_t work_bytes, sc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(FlatApply<T, NDIM, R, CLS>::NTHR)
   const int x0 = blockIdx.x * K::BX;
   const int y0 = NDIM == 3 ? blockIdx.y * K::BY : 0;
   const int z0 = (NDIM == 3 ? blockIdx.z : blockIdx.y) * g.H;
-  K::run_tile(x, y, g, W, x0, y0, z0, smem);
+  StoreEpi<T, NDIM, K::VX> epi{y, &g};
+  K::run_tile(x, g, W, x0, y0, z0, smem, epi);
 }
 
 static int g_num_sms = 0;

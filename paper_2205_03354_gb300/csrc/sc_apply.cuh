@@ -102,7 +102,8 @@ struct FlatApply {
   }
 
   // Stages input plane `zs` (output coordinate along S, may be outside the
-  // grid) of the tile (x0, y0) into `buf` with cp.async.
+  // grid) of the tile (x0, y0) into `buf`: 16-byte cp.async.cg chunks (L2,
+  // zero-filled outside the grid) when aligned, else element loads.
   static __device__ __forceinline__ void load_plane(const T *__restrict__ x, const ApplyGeom &g,
                                                     int x0, int y0, int zs, T *buf,
                                                     const int *coff) {
@@ -128,8 +129,8 @@ struct FlatApply {
         int iy = 0;
         if (NDIM == 3) iy = map_coord(y0 - RP + r, g.ny, g.bc, R);
         const bool ok = (iz >= 0) & (ix >= 0) & (iy >= 0);
-        const T *src = ok ? x + pbase + (long long)iy * g.in_sy + ix : x;
-        cp_async_elem<sizeof(T)>(buf + e, src, ok ? int(sizeof(T)) : 0);
+        // plain L2 loads (not L1): persistent solvers rewrite x between tiles
+        buf[e] = ok ? __ldcg(x + pbase + (long long)iy * g.in_sy + ix) : T(0);
       }
     }
   }
@@ -153,11 +154,13 @@ struct FlatApply {
     }
   }
 
-  // One tile: outputs [x0, x0+BX) x [y0, y0+BY) x planes [z0, z0+H).
-  static __device__ __forceinline__ void run_tile(const T *__restrict__ x, T *__restrict__ y,
-                                                  const ApplyGeom &g,
-                                                  const BoxWeights<T, NDIM, R> &W, int x0,
-                                                  int y0, int z0, T *smem) {
+  // One tile: outputs [x0, x0+BX) x [y0, y0+BY) x planes [z0, z0+H).  WT
+  // holds the dense weight box (member array w), EPI consumes every
+  // completed run of VX outputs: epi(plane, row, first column, values).
+  template <class WT, class EPI>
+  static __device__ __forceinline__ void run_tile(const T *__restrict__ x, const ApplyGeom &g,
+                                                  const WT &W, int x0, int y0, int z0, T *smem,
+                                                  EPI &epi) {
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int ns = NDIM == 3 ? g.nz : g.ny;
     const int zend = min(z0 + g.H, ns);
@@ -227,27 +230,7 @@ struct FlatApply {
             for (int vy = 0; vy < VY; ++vy) {
               const int yy = NDIM == 3 ? y0 + ty * VY + vy : 0;
               if (NDIM == 3 && yy >= g.ny) continue;
-              T *dst = y + (long long)j * (NDIM == 3 ? g.out_ss : g.out_sy) +
-                       (NDIM == 3 ? (long long)yy * g.out_sy : 0) + xo;
-              if (g.vec && xo + VX <= g.nx) {
-                if (sizeof(T) * VX == 16) {
-                  if (sizeof(T) == 4) {
-                    float4 v = make_float4(float(acc[sc_][vy][0]), float(acc[sc_][vy][1 % VX]),
-                                           float(acc[sc_][vy][2 % VX]), float(acc[sc_][vy][3 % VX]));
-                    *reinterpret_cast<float4 *>(dst) = v;
-                  } else {
-                    double2 v = make_double2(double(acc[sc_][vy][0]), double(acc[sc_][vy][1 % VX]));
-                    *reinterpret_cast<double2 *>(dst) = v;
-                  }
-                } else {
-#pragma unroll
-                  for (int vx = 0; vx < VX; ++vx) dst[vx] = acc[sc_][vy][vx];
-                }
-              } else {
-#pragma unroll
-                for (int vx = 0; vx < VX; ++vx)
-                  if (xo + vx < g.nx) dst[vx] = acc[sc_][vy][vx];
-              }
+              epi(j, yy, xo, acc[sc_][vy]);
             }
           }
 #pragma unroll
@@ -259,6 +242,29 @@ struct FlatApply {
     }
     cp_async_wait<0>();
     __syncthreads();  // the ring may be reused by the caller
+  }
+};
+
+// Stores the outputs: y = acc (a plain apply).
+template <typename T, int NDIM, int VX>
+struct StoreEpi {
+  T *__restrict__ y;
+  const ApplyGeom *g;
+  __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX]) const {
+    T *dst = y + (long long)j * (NDIM == 3 ? g->out_ss : g->out_sy) +
+             (NDIM == 3 ? (long long)yy * g->out_sy : 0) + xo;
+    if (g->vec && xo + VX <= g->nx && sizeof(T) * VX == 16) {
+      if (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(dst) =
+            make_float4(float(v[0]), float(v[1 % VX]), float(v[2 % VX]), float(v[3 % VX]));
+      } else {
+        *reinterpret_cast<double2 *>(dst) = make_double2(double(v[0]), double(v[1 % VX]));
+      }
+    } else {
+#pragma unroll
+      for (int vx = 0; vx < VX; ++vx)
+        if (xo + vx < g->nx) dst[vx] = v[vx];
+    }
   }
 };
 

@@ -1,0 +1,774 @@
+// Solver entry points: the biharmonic plate problem (Sec. 3.3), semi-implicit
+// Cahn-Hilliard steps (Sec. 4) and their batched form, on top of the
+// persistent CG engine of sc_solver.cuh and a host-driven plain CG.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sc_apply_host.h"
+#include "sc_internal.h"
+#include "sc_solver.cuh"
+#include "sc_solver_host.h"
+
+namespace sc {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+template <typename TI, int R>
+__global__ void __launch_bounds__(CG_NTHR)
+    cg_persistent_kernel(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob,
+                         long long budget) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[CG_NTHR / 32];
+  __shared__ int flag;
+  const int pi = cta_prob[blockIdx.x];
+  if (pi < 0) return;
+  const SolveProb &P = probs[pi];
+  if (P.st->phase == 2) return;
+  GroupCtx G{&P, int(blockIdx.x) - P.cta0, 0u, 0u, red, &flag};
+  if (P.ndim == 2)
+    cg_run<TI, 2, R>(G, smem, budget);
+  else
+    cg_run<TI, 3, R>(G, smem, budget);
+}
+
+// out = ring of g (padded array), interior set to zero.
+__global__ void k_ring_copy(const double *__restrict__ g, double *__restrict__ out, int ndim,
+                            long long px, long long py, long long pz, int R) {
+  const long long n = px * py * pz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long ix = i % px, iy = (i / px) % py, iz = i / (px * py);
+    bool inner = ix >= R && ix < px - R && iy >= R && iy < py - R;
+    if (ndim == 3) inner = inner && iz >= R && iz < pz - R;
+    out[i] = inner ? 0.0 : g[i];
+  }
+}
+
+// y = f - y
+__global__ void k_sub_from(double *__restrict__ y, const double *__restrict__ f, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = f[i] - y[i];
+}
+
+// y = u + c * y
+__global__ void k_u_plus_cy(double *__restrict__ y, const double *__restrict__ u, double c, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(c, y[i], u[i]);
+}
+
+// g = f'(u)
+__global__ void k_fprime(const double *__restrict__ u, double *__restrict__ g, long long n, int chem,
+                         double rho, double ca, double cb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double c = u[i];
+    g[i] = chem == 0 ? c * c * c - c : 2.0 * rho * (c - ca) * (c - cb) * (2.0 * c - ca - cb);
+  }
+}
+
+// ---- plain CG helpers (one kernel per operation) --------------------------
+constexpr int PL_NTHR = 256;
+constexpr int PL_CHUNK = PL_NTHR * 16;
+
+__global__ void k_dot_part(const double *__restrict__ a, const double *__restrict__ b, long long n,
+                           double *__restrict__ part) {
+  __shared__ double red[PL_NTHR / 32];
+  const long long e0 = (long long)blockIdx.x * PL_CHUNK, e1 = min(e0 + PL_CHUNK, n);
+  double s = 0.0;
+  for (long long i = e0 + threadIdx.x; i < e1; i += PL_NTHR) s += a[i] * b[i];
+  s = block_sum<PL_NTHR>(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// scal[slot] = sum(part[0..n)) in index order
+__global__ void k_sum_final(const double *__restrict__ part, int n, double *__restrict__ scal, int slot) {
+  __shared__ double red[PL_NTHR / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += PL_NTHR) s += part[i];
+  s = block_sum<PL_NTHR>(s, red);
+  if (threadIdx.x == 0) scal[slot] = s;
+}
+
+// scalar slots: 0 rr, 1 pq, 2 rr_new, 3 alpha, 4 beta, 5 bnorm^2, 6 converged flag, 7 breakdown
+__global__ void k_alpha(double *s) {
+  const double pq = s[1];
+  if (!(pq > 0.0) || !(pq < 1e300)) {
+    s[7] = 1.0;
+    s[3] = 0.0;
+  } else {
+    s[3] = s[0] / pq;
+  }
+}
+__global__ void k_beta(double *s, double tol) {
+  s[4] = s[2] / s[0];
+  s[0] = s[2];
+  if (sqrt(s[2]) <= tol * sqrt(s[5])) s[6] = 1.0;
+  if (!(s[2] == s[2])) s[7] = 1.0;
+}
+__global__ void k_xr_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                            const double *__restrict__ q, const double *__restrict__ s, long long n) {
+  const double al = s[3];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    r[i] -= al * q[i];
+  }
+}
+__global__ void k_p_update(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ s,
+                           long long n) {
+  const double be = s[4];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = r[i] + be * p[i];
+}
+// q = a p + b q
+__global__ void k_axpby(double *__restrict__ q, const double *__restrict__ p, double a, double b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    q[i] = fma(b, q[i], a * p[i]);
+}
+__global__ void k_add_const(double *__restrict__ x, const double *__restrict__ s, int num, int den_slot,
+                            long long n) {
+  const double c = (s[num] - s[den_slot]) / double(n);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] += c;
+}
+
+// ---- Cahn-Hilliard statistics ---------------------------------------------
+__global__ void k_ch_stats_part(const double *__restrict__ u, int ndim, int nx, int ny, int nz, double h,
+                                double kappa, int chem, double rho, double ca, double cb,
+                                double *__restrict__ pm, double *__restrict__ pe) {
+  __shared__ double red[PL_NTHR / 32];
+  const long long n = (long long)nx * ny * (ndim == 3 ? nz : 1);
+  const long long e0 = (long long)blockIdx.x * PL_CHUNK, e1 = min(e0 + PL_CHUNK, n);
+  double m = 0.0, e = 0.0;
+  for (long long i = e0 + threadIdx.x; i < e1; i += PL_NTHR) {
+    const int ix = int(i % nx), iy = int((i / nx) % ny), iz = ndim == 3 ? int(i / ((long long)nx * ny)) : 0;
+    const double c = u[i];
+    m += c;
+    const double f = chem == 0 ? (c * c - 1.0) * (c * c - 1.0) / 4.0
+                               : rho * (c - ca) * (c - ca) * (c - cb) * (c - cb);
+    double g2 = 0.0;
+    const long long bz = (long long)iz * nx * ny;
+    double d = (u[bz + (long long)iy * nx + (ix + 1 == nx ? 0 : ix + 1)] - c) / h;
+    g2 += d * d;
+    d = (u[bz + (long long)(iy + 1 == ny ? 0 : iy + 1) * nx + ix] - c) / h;
+    g2 += d * d;
+    if (ndim == 3) {
+      d = (u[(long long)(iz + 1 == nz ? 0 : iz + 1) * nx * ny + (long long)iy * nx + ix] - c) / h;
+      g2 += d * d;
+    }
+    e += f + 0.5 * kappa * g2;
+  }
+  m = block_sum<PL_NTHR>(m, red);
+  if (threadIdx.x == 0) pm[blockIdx.x] = m;
+  e = block_sum<PL_NTHR>(e, red);
+  if (threadIdx.x == 0) pe[blockIdx.x] = e;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct Carver {
+  char *base;
+  size_t off = 0, cap;
+  Carver(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+  void *take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void *p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+  bool ok() const { return base == nullptr || off <= cap; }
+};
+
+template <typename T, int NDIM, int R>
+static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
+  using K = FlatApply<T, NDIM, R, CLS_CROSS2>;
+  const long long nx = sp.n[0], ny = sp.n[1], nz = NDIM == 3 ? sp.n[2] : 1;
+  const long long txy = ((nx + K::BX - 1) / K::BX) * (NDIM == 3 ? (ny + K::BY - 1) / K::BY : 1);
+  const long long planes = NDIM == 3 ? nz : ny;
+  const long long npts = nx * ny * nz;
+  const long long target = std::max<long long>(1, npts / 16384);
+  long long h = (txy * planes + target - 1) / target;
+  h = std::max<long long>(4, std::min<long long>(h, 128));
+  h = std::min<long long>(h, planes);
+  H = int(h);
+  ntiles = int(txy * ((planes + h - 1) / h));
+}
+
+static size_t smem_bytes_cg() {
+  size_t m = 0;
+  m = std::max(m, FlatApply<float, 2, 2, CLS_CROSS2>::SMEM);
+  m = std::max(m, FlatApply<float, 3, 2, CLS_CROSS2>::SMEM);
+  m = std::max(m, FlatApply<double, 2, 2, CLS_CROSS2>::SMEM);
+  m = std::max(m, FlatApply<double, 3, 2, CLS_CROSS2>::SMEM);
+  return m;
+}
+
+// Lays out one problem's work space; with base == nullptr only sizes.
+static void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
+  std::memset(&P, 0, sizeof(P));
+  const long long npts = sp.n[0] * sp.n[1] * (sp.ndim == 3 ? sp.n[2] : 1);
+  P.ndim = sp.ndim;
+  P.nx = int(sp.n[0]);
+  P.ny = int(sp.n[1]);
+  P.nz = sp.ndim == 3 ? int(sp.n[2]) : 1;
+  P.bc = sp.bc;
+  P.npts = npts;
+  if (sp.ndim == 2) {
+    tiles_for<float, 2, 2>(sp, P.H_in, P.ntiles_in);
+    if (!sp.mixed) tiles_for<double, 2, 2>(sp, P.H_in, P.ntiles_in);
+    tiles_for<double, 2, 2>(sp, P.H_64, P.ntiles_64);
+  } else {
+    tiles_for<float, 3, 2>(sp, P.H_in, P.ntiles_in);
+    if (!sp.mixed) tiles_for<double, 3, 2>(sp, P.H_in, P.ntiles_in);
+    tiles_for<double, 3, 2>(sp, P.H_64, P.ntiles_64);
+  }
+  P.nchunks = int((npts + CG_CHUNK - 1) / CG_CHUNK);
+  P.nslot = std::max({P.ntiles_in, P.ntiles_64, P.nchunks});
+  P.a = sp.a;
+  P.b = sp.b;
+  P.mixed = sp.mixed;
+  P.mean_fix = sp.mean_fix;
+  P.rtol = sp.rtol;
+  P.delta = 0.1;
+  P.maxit = sp.maxit;
+  const size_t ti = sp.mixed ? 4 : 8;
+  P.x = sp.x;
+  P.rhs = static_cast<double *>(cv.take(npts * 8));
+  P.r = static_cast<double *>(cv.take(npts * 8));
+  if (sp.mixed) {
+    P.rh = cv.take(npts * ti);
+    P.d = cv.take(npts * ti);
+  } else {
+    P.rh = P.r;
+    P.d = P.x;
+  }
+  P.p = cv.take(npts * ti);
+  P.q = cv.take(npts * ti);
+  P.part = static_cast<double *>(cv.take(size_t(3) * P.nslot * 8));
+  P.scal = static_cast<double *>(cv.take(8 * 8));
+  P.bar = static_cast<unsigned *>(cv.take(16));
+  P.st = static_cast<SolveState *>(cv.take(sizeof(SolveState)));
+  const int nbox = sp.ndim == 3 ? 125 : 25;
+  P.w64 = static_cast<const double *>(cv.take(nbox * 8));
+  P.wT = cv.take(nbox * 8);
+  aux.nbox = nbox;
+  // scratch for problem set-up (ring copy of the padded grid)
+  long long padded = 1;
+  for (int a = 0; a < sp.ndim; ++a) padded *= sp.n[a] + 2 * sp.R;
+  aux.scratch = static_cast<double *>(cv.take(std::max<long long>(padded, npts) * 8));
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Fills the dense weight boxes of B (composed Lap o Lap, exact weights) and
+// the state on the device (asynchronously from pageable host buffers).
+static int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
+  sc_stencil L, B;
+  int rc = sc_laplacian(sp.ndim, sp.order, &L);
+  if (!rc) rc = sc_compose_stencil(&L, &L, &B);
+  if (rc) return rc;
+  std::vector<double> w(B.npts);
+  if ((rc = weights_f64(&B, sp.h_num, sp.h_den, w.data()))) return rc;
+  const int R = 2, Wd = 2 * R + 1;
+  std::vector<double> box(aux.nbox, 0.0);
+  std::vector<float> boxf(aux.nbox * 2, 0.0f);  // room for a double box too
+  for (int k = 0; k < B.npts; ++k) {
+    const int dx = B.off[k][0], dy = B.off[k][1], dz = B.off[k][2];
+    const int idx = sp.ndim == 3 ? ((dz + R) * Wd + (dy + R)) * Wd + (dx + R) : (dy + R) * Wd + (dx + R);
+    box[idx] = w[k];
+  }
+  cudaMemcpyAsync(const_cast<double *>(P.w64), box.data(), aux.nbox * 8, cudaMemcpyHostToDevice, st);
+  if (P.mixed) {
+    std::vector<float> wf(B.npts);
+    if ((rc = weights_f32(&B, sp.h_num, sp.h_den, wf.data()))) return rc;
+    for (int k = 0; k < B.npts; ++k) {
+      const int dx = B.off[k][0], dy = B.off[k][1], dz = B.off[k][2];
+      const int idx = sp.ndim == 3 ? ((dz + R) * Wd + (dy + R)) * Wd + (dx + R) : (dy + R) * Wd + (dx + R);
+      boxf[idx] = wf[k];
+    }
+    cudaMemcpyAsync(const_cast<void *>(P.wT), boxf.data(), aux.nbox * 4, cudaMemcpyHostToDevice, st);
+  } else {
+    cudaMemcpyAsync(const_cast<void *>(P.wT), box.data(), aux.nbox * 8, cudaMemcpyHostToDevice, st);
+  }
+  SolveState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  cudaMemcpyAsync(P.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, st);
+  // 16-byte tile loads need aligned vectors and rows
+  const bool al = aligned16(P.x) && aligned16(P.p) && aligned16(P.r);
+  P.vec_in = al && (P.nx % (P.mixed ? 4 : 2) == 0);
+  P.vec_64 = al && (P.nx % 2 == 0);
+  cudaError_t e = cudaStreamSynchronize(st);  // host buffers above are locals
+  if (e != cudaSuccess) return fail(SC_ECUDA, "upload: %s", cudaGetErrorString(e));
+  return SC_OK;
+}
+
+static int grid1d(long long n) { return int(std::min<long long>((n + 255) / 256, 8LL * num_sms())); }
+
+// Right-hand side of the plate problem: rhs = g - A(ring), x = 0.
+static int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
+  const int R = sp.R;
+  long long p[3] = {1, 1, 1};
+  for (int a = 0; a < sp.ndim; ++a) p[a] = sp.n[a] + 2 * R;
+  const long long np = p[0] * p[1] * p[2];
+  k_ring_copy<<<grid1d(np), 256, 0, st>>>(bp->ghost_dev, aux.scratch, sp.ndim, p[0], p[1], p[2], R);
+  sc_stencil L, B;
+  sc_laplacian(sp.ndim, sp.order, &L);
+  sc_compose_stencil(&L, &L, &B);
+  ApplyReq q{&B, SC_F64, SC_BC_GHOSTED, sp.n, sp.h_num, sp.h_den, aux.scratch, P.rhs};
+  if (int rc = apply_enqueue(q, st)) return rc;
+  k_sub_from<<<grid1d(P.npts), 256, 0, st>>>(P.rhs, bp->f_dev, P.npts);
+  cudaMemsetAsync(P.x, 0, P.npts * 8, st);
+  return SC_OK;
+}
+
+// Right-hand side of a Cahn-Hilliard step: rhs = u + dt M Lap(f'(u)).
+static int setup_ch(const sc_ch *cp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
+  k_fprime<<<grid1d(P.npts), 256, 0, st>>>(P.x, aux.scratch, P.npts, cp->chem, cp->rho, cp->ca, cp->cb);
+  sc_stencil L;
+  sc_laplacian(sp.ndim, sp.order, &L);
+  ApplyReq q{&L, SC_F64, SC_BC_PERIODIC, sp.n, sp.h_num, sp.h_den, aux.scratch, P.rhs};
+  if (int rc = apply_enqueue(q, st)) return rc;
+  k_u_plus_cy<<<grid1d(P.npts), 256, 0, st>>>(P.rhs, P.x, cp->dt * cp->M, P.npts);
+  return SC_OK;
+}
+
+// Assigns CTA groups for problems[first..last) and launches one cooperative
+// persistent kernel for them.
+template <typename TI>
+static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx, SolveProb *dprobs,
+                        int *dmap, unsigned *dbars, cudaStream_t st, long long budget) {
+  auto kern = cg_persistent_kernel<TI, 2>;
+  const size_t smem = smem_bytes_cg();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    attr = true;
+  }
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, CG_NTHR, smem);
+  if (nb < 1) return fail(SC_ECUDA, "persistent CG kernel does not fit on an SM");
+  const int G = nb * num_sms();
+  // proportional split of the CTAs by problem size, at least one each,
+  // at most the problem's number of work units
+  double wsum = 0.0;
+  for (int i : idx) wsum += double(hp[i].npts);
+  int used = 0;
+  std::vector<int> nc(idx.size());
+  for (size_t k = 0; k < idx.size(); ++k) {
+    const SolveProb &P = hp[idx[k]];
+    const int units = std::max({P.ntiles_in, P.ntiles_64, P.nchunks});
+    int c = int(std::floor(double(G - int(idx.size())) * double(P.npts) / wsum)) + 1;
+    c = std::max(1, std::min(c, units));
+    nc[k] = c;
+    used += c;
+  }
+  if (used > G) return fail(SC_EINVAL, "internal: CTA assignment exceeds the grid");
+  std::vector<int> map(used, -1);
+  int c0 = 0;
+  for (size_t k = 0; k < idx.size(); ++k) {
+    SolveProb &P = hp[idx[k]];
+    P.cta0 = c0;
+    P.ncta = nc[k];
+    P.bar = dbars + 2 * idx[k];
+    for (int j = 0; j < nc[k]; ++j) map[c0 + j] = idx[k];
+    c0 += nc[k];
+  }
+  cudaMemcpyAsync(dprobs, hp.data(), hp.size() * sizeof(SolveProb), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(dbars, 0, hp.size() * 2 * sizeof(unsigned), st);
+  const SolveProb *a0 = dprobs;
+  const int *a1 = dmap;
+  long long a2 = budget;
+  void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(used), dim3(CG_NTHR), args, smem, st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "cooperative launch: %s", cudaGetErrorString(e));
+  // pageable sources above: finish before the vectors go out of scope
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "persistent CG: %s", cudaGetErrorString(e));
+  return SC_OK;
+}
+
+int max_group_ctas(bool mixed) {
+  const size_t smem = smem_bytes_cg();
+  int nb = 0;
+  if (mixed)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_persistent_kernel<float, 2>, CG_NTHR, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_persistent_kernel<double, 2>, CG_NTHR, smem);
+  return std::max(1, nb) * num_sms();
+}
+
+// Runs every problem to completion (waves of at most one CTA per problem
+// beyond the grid size).
+int run_persistent(std::vector<SolveProb> &hp, SolveProb *dprobs, int *dmap, unsigned *dbars,
+                   cudaStream_t st, long long budget) {
+  for (int mixed = 0; mixed < 2; ++mixed) {
+    std::vector<int> all;
+    for (size_t i = 0; i < hp.size(); ++i)
+      if (hp[i].mixed == mixed) all.push_back(int(i));
+    const int G = max_group_ctas(mixed);
+    for (size_t w0 = 0; w0 < all.size(); w0 += size_t(G)) {
+      std::vector<int> idx(all.begin() + w0, all.begin() + std::min(all.size(), w0 + size_t(G)));
+      int rc = mixed ? launch_group<float>(hp, idx, dprobs, dmap, dbars, st, budget)
+                     : launch_group<double>(hp, idx, dprobs, dmap, dbars, st, budget);
+      if (rc) return rc;
+    }
+  }
+  return SC_OK;
+}
+
+// Host-driven FP64 CG, one kernel per operation (the plain comparison path).
+static int run_plain(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st,
+                     double *scal_host) {
+  const long long n = P.npts;
+  const int nblk = int((n + PL_CHUNK - 1) / PL_CHUNK);
+  double *part = P.part;  // >= nchunks slots (PL_CHUNK == CG_CHUNK)
+  double *s = P.scal;
+  sc_stencil L, B;
+  sc_laplacian(sp.ndim, sp.order, &L);
+  sc_compose_stencil(&L, &L, &B);
+  const int g = grid1d(n);
+  auto apply_op = [&](const double *in, double *out) -> int {
+    ApplyReq q{&B, SC_F64, sp.bc, sp.n, sp.h_num, sp.h_den, in, out};
+    if (int rc = apply_enqueue(q, st)) return rc;
+    if (P.a != 0.0 || P.b != 1.0) k_axpby<<<g, 256, 0, st>>>(out, in, P.a, P.b, n);
+    return SC_OK;
+  };
+  auto dot = [&](const double *a, const double *b, int slot) {
+    k_dot_part<<<nblk, PL_NTHR, 0, st>>>(a, b, n, part);
+    k_sum_final<<<1, PL_NTHR, 0, st>>>(part, nblk, s, slot);
+  };
+  double *p = static_cast<double *>(P.p), *q = static_cast<double *>(P.q), *r = P.r;
+  cudaMemsetAsync(s, 0, 8 * 8, st);
+  // r = rhs - A x
+  if (int rc = apply_op(P.x, r)) return rc;
+  k_sub_from<<<g, 256, 0, st>>>(r, P.rhs, n);
+  cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, st);
+  dot(r, r, 0);
+  dot(P.rhs, P.rhs, 5);
+  double hs[8];
+  cudaMemcpyAsync(hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  long long it = 0;
+  int status = SC_OK;
+  const double tol = sp.rtol;
+  bool conv = std::sqrt(hs[0]) <= tol * std::sqrt(hs[5]);
+  while (!conv) {
+    if (it >= sp.maxit) {
+      status = SC_ENOTCONV;
+      break;
+    }
+    if (int rc = apply_op(p, q)) return rc;
+    dot(p, q, 1);
+    k_alpha<<<1, 1, 0, st>>>(s);
+    k_xr_update<<<g, 256, 0, st>>>(P.x, r, p, q, s, n);
+    dot(r, r, 2);
+    k_beta<<<1, 1, 0, st>>>(s, tol);
+    k_p_update<<<g, 256, 0, st>>>(p, r, s, n);
+    ++it;
+    if ((it & 7) == 0 || it >= sp.maxit) {
+      cudaMemcpyAsync(hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      if (hs[7] != 0.0) {
+        status = SC_EBREAKDOWN;
+        break;
+      }
+      conv = hs[6] != 0.0;
+    }
+  }
+  if (P.mean_fix) {
+    k_dot_part<<<nblk, PL_NTHR, 0, st>>>(P.rhs, aux.ones, n, part);
+    k_sum_final<<<1, PL_NTHR, 0, st>>>(part, nblk, s, 0);
+    k_dot_part<<<nblk, PL_NTHR, 0, st>>>(P.x, aux.ones, n, part);
+    k_sum_final<<<1, PL_NTHR, 0, st>>>(part, nblk, s, 1);
+    k_add_const<<<g, 256, 0, st>>>(P.x, s, 0, 1, n);
+  }
+  // true residual
+  if (int rc = apply_op(P.x, r)) return rc;
+  k_sub_from<<<g, 256, 0, st>>>(r, P.rhs, n);
+  dot(r, r, 2);
+  cudaMemcpyAsync(hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "plain CG: %s", cudaGetErrorString(e));
+  const double bn = std::sqrt(hs[5]);
+  scal_host[0] = double(it);
+  scal_host[1] = bn > 0 ? std::sqrt(hs[2]) / bn : 0.0;
+  if (status == SC_OK && !(scal_host[1] <= tol)) status = SC_ENOTCONV;
+  scal_host[2] = double(status);
+  return SC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// problem specs from the public structs
+// ---------------------------------------------------------------------------
+
+double kappa_estimate(const ProbSpec &sp, double h) {
+  const double d = sp.ndim;
+  if (sp.bc == SC_BC_PERIODIC) {  // I + s B, eigenvalues 1 .. 1 + s (4d/h^2)^2
+    const double lm = 4.0 * d / (h * h);
+    return 1.0 + sp.b * lm * lm;
+  }
+  const double lmax = 4.0 * d / (h * h), lmin = d * M_PI * M_PI;  // Dirichlet-like Laplacian
+  return (lmax / lmin) * (lmax / lmin);
+}
+
+static int choose_prec(int req, double kappa) {
+  if (req == SC_PREC_F64 || req == SC_PREC_MIXED) return req;
+  return kappa * std::ldexp(1.0, -24) <= 1e-2 ? SC_PREC_MIXED : SC_PREC_F64;
+}
+
+int bvp_spec(const sc_bvp *b, ProbSpec &sp) {
+  if (!b) return fail(SC_EINVAL, "null problem");
+  if (b->ndim != 2 && b->ndim != 3) return fail(SC_EINVAL, "ndim must be 2 or 3");
+  if (b->order != 2) return fail(SC_EINVAL, "the solvers support the order-2 Laplacian (13/25-point Lap o Lap)");
+  for (int a = 0; a < b->ndim; ++a)
+    if (b->n[a] != b->n[0] || b->n[a] < 1 || b->n[a] > 65536) return fail(SC_EINVAL, "n must be equal per axis, 1..65536");
+  if (!(b->rtol > 0.0) || b->maxit < 0) return fail(SC_EINVAL, "bad rtol/maxit");
+  if (b->solver != SC_SOLVER_PERSISTENT && b->solver != SC_SOLVER_PLAIN) return fail(SC_EINVAL, "bad solver");
+  if (b->prec < 0 || b->prec > 2) return fail(SC_EINVAL, "bad prec");
+  if (!b->f_dev || !b->ghost_dev || !b->x_dev) return fail(SC_EINVAL, "null device pointer");
+  std::memset(&sp, 0, sizeof(sp));
+  sp.ndim = b->ndim;
+  sp.order = b->order;
+  sp.R = 2;
+  for (int a = 0; a < 3; ++a) sp.n[a] = a < b->ndim ? b->n[a] : 1;
+  sp.bc = SC_BC_ZERO;
+  sp.h_num = 1;
+  sp.h_den = b->n[0] + 1;
+  sp.a = 0.0;
+  sp.b = 1.0;
+  sp.rtol = b->rtol;
+  sp.maxit = b->maxit;
+  sp.x = b->x_dev;
+  sp.mean_fix = 0;
+  const int prec = choose_prec(b->prec, kappa_estimate(sp, 1.0 / double(b->n[0] + 1)));
+  sp.mixed = prec == SC_PREC_MIXED && b->solver == SC_SOLVER_PERSISTENT;
+  sp.solver = b->solver;
+  return SC_OK;
+}
+
+int ch_spec(const sc_ch *c, int item, double *u, ProbSpec &sp) {
+  std::memset(&sp, 0, sizeof(sp));
+  sp.ndim = c->ndim;
+  sp.order = c->order;
+  sp.R = 2;
+  for (int a = 0; a < 3; ++a) sp.n[a] = a < c->ndim ? c->n[a] : 1;
+  sp.bc = SC_BC_PERIODIC;
+  sp.h_num = c->h_num;
+  sp.h_den = c->h_den;
+  sp.a = 1.0;
+  sp.b = c->dt * c->M * c->kappa;
+  sp.rtol = c->rtol;
+  sp.maxit = c->maxit;
+  const long long npts = sp.n[0] * sp.n[1] * sp.n[2];
+  sp.x = u + (long long)item * npts;
+  sp.mean_fix = 1;
+  const int prec = choose_prec(c->prec, kappa_estimate(sp, double(c->h_num) / double(c->h_den)));
+  sp.mixed = prec == SC_PREC_MIXED && c->solver == SC_SOLVER_PERSISTENT;
+  sp.solver = c->solver;
+  (void)item;
+  return SC_OK;
+}
+
+static int ch_validate(const sc_ch *c) {
+  if (!c) return fail(SC_EINVAL, "null problem");
+  if (c->ndim != 2 && c->ndim != 3) return fail(SC_EINVAL, "ndim must be 2 or 3");
+  if (c->order != 2) return fail(SC_EINVAL, "the solvers support the order-2 Laplacian");
+  for (int a = 0; a < c->ndim; ++a)
+    if (c->n[a] != c->n[0] || c->n[a] < 4 || c->n[a] > 65536) return fail(SC_EINVAL, "n must be equal per axis, 4..65536");
+  if (c->batch < 1 || c->batch > 4096) return fail(SC_EINVAL, "batch out of range");
+  if (c->h_num <= 0 || c->h_den <= 0) return fail(SC_EINVAL, "h must be positive");
+  if (!(c->dt > 0.0) || !(c->M > 0.0) || !(c->kappa > 0.0)) return fail(SC_EINVAL, "dt, M, kappa must be positive");
+  if (c->chem != 0 && c->chem != 1) return fail(SC_EINVAL, "chem must be 0 or 1");
+  if (!(c->rtol > 0.0) || c->maxit < 0) return fail(SC_EINVAL, "bad rtol/maxit");
+  if (c->solver != SC_SOLVER_PERSISTENT && c->solver != SC_SOLVER_PLAIN) return fail(SC_EINVAL, "bad solver");
+  if (c->prec < 0 || c->prec > 2) return fail(SC_EINVAL, "bad prec");
+  return SC_OK;
+}
+
+// Work space of a set of problems: per-problem areas + batch descriptors.
+size_t batch_bytes(const std::vector<ProbSpec> &sps) {
+  Carver cv(nullptr, 0);
+  for (const ProbSpec &sp : sps) {
+    SolveProb P;
+    ProbAux aux;
+    layout(sp, cv, P, aux);
+    cv.take(std::max<long long>(P.npts, 1) * 8);  // ones vector (plain mean fix)
+  }
+  cv.take(sps.size() * sizeof(SolveProb));
+  cv.take(sizeof(int) * size_t(8) * 1024 * 16);  // CTA map (max grid)
+  cv.take(sps.size() * 2 * sizeof(unsigned));
+  return cv.off + 256;
+}
+
+__global__ void k_fill(double *x, double v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+// Sets up, solves and reports a set of problems.  setup(i, P, aux) enqueues
+// the right-hand side (and initial guess) of problem i.
+template <class SETUP>
+int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solve_info *infos,
+              cudaStream_t st, SETUP setup) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!work) return fail(SC_EINVAL, "null work space");
+  const size_t need = batch_bytes(sps);
+  if (work_bytes < need) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, need);
+  Carver cv(work, work_bytes);
+  std::vector<SolveProb> hp(sps.size());
+  std::vector<ProbAux> aux(sps.size());
+  for (size_t i = 0; i < sps.size(); ++i) {
+    layout(sps[i], cv, hp[i], aux[i]);
+    aux[i].ones = static_cast<double *>(cv.take(std::max<long long>(hp[i].npts, 1) * 8));
+  }
+  SolveProb *dprobs = static_cast<SolveProb *>(cv.take(sps.size() * sizeof(SolveProb)));
+  int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(8) * 1024 * 16));
+  unsigned *dbars = static_cast<unsigned *>(cv.take(sps.size() * 2 * sizeof(unsigned)));
+  for (size_t i = 0; i < sps.size(); ++i) {
+    if (int rc = upload_prob(sps[i], hp[i], aux[i], st)) return rc;
+    if (int rc = setup(int(i), hp[i], aux[i])) return rc;
+  }
+  std::vector<double> plain_res(3 * sps.size(), 0.0);
+  bool any_persistent = false;
+  for (size_t i = 0; i < sps.size(); ++i) {
+    if (sps[i].solver == SC_SOLVER_PLAIN) {
+      k_fill<<<grid1d(hp[i].npts), 256, 0, st>>>(aux[i].ones, 1.0, hp[i].npts);
+      if (int rc = run_plain(sps[i], hp[i], aux[i], st, &plain_res[3 * i])) return rc;
+    } else {
+      any_persistent = true;
+    }
+  }
+  if (any_persistent) {
+    std::vector<SolveProb> sub;
+    std::vector<int> back;
+    for (size_t i = 0; i < sps.size(); ++i)
+      if (sps[i].solver != SC_SOLVER_PLAIN) {
+        sub.push_back(hp[i]);
+        back.push_back(int(i));
+      }
+    if (int rc = run_persistent(sub, dprobs, dmap, dbars, st, LLONG_MAX)) return rc;
+    for (size_t k = 0; k < sub.size(); ++k) hp[back[k]] = sub[k];
+  }
+  std::vector<SolveState> hs(sps.size());
+  for (size_t i = 0; i < sps.size(); ++i)
+    if (sps[i].solver != SC_SOLVER_PLAIN)
+      cudaMemcpyAsync(&hs[i], hp[i].st, sizeof(SolveState), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "solve: %s", cudaGetErrorString(e));
+  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (size_t i = 0; i < sps.size(); ++i) {
+    sc_solve_info &in = infos[i];
+    std::memset(&in, 0, sizeof(in));
+    in.prec = sps[i].mixed ? SC_PREC_MIXED : SC_PREC_F64;
+    in.seconds = sec;
+    if (sps[i].solver == SC_SOLVER_PLAIN) {
+      in.iters = (long long)plain_res[3 * i];
+      in.rel_res = plain_res[3 * i + 1];
+      in.status = int(plain_res[3 * i + 2]);
+    } else {
+      in.iters = hs[i].iters;
+      in.outer = hs[i].outer;
+      in.rel_res = hs[i].rel;
+      in.status = hs[i].phase == 2 ? hs[i].status : SC_ETIMEOUT;
+    }
+  }
+  clear_error();
+  return SC_OK;
+}
+
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+size_t sc_bvp_batch_work_bytes(const sc_bvp *probs, int32_t count) {
+  if (!probs || count < 1) return 0;
+  std::vector<ProbSpec> sps(count);
+  for (int i = 0; i < count; ++i)
+    if (bvp_spec(&probs[i], sps[i])) return 0;
+  return batch_bytes(sps);
+}
+
+size_t sc_bvp_work_bytes(const sc_bvp *p) { return sc_bvp_batch_work_bytes(p, 1); }
+
+int sc_solve_biharmonic_batch(const sc_bvp *probs, int32_t count, void *work_dev, size_t work_bytes,
+                              sc_solve_info *infos, sc_stream_t stream) {
+  if (!probs || count < 1 || !infos) return fail(SC_EINVAL, "bad batch arguments");
+  std::vector<ProbSpec> sps(count);
+  for (int i = 0; i < count; ++i)
+    if (int rc = bvp_spec(&probs[i], sps[i])) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return solve_set(sps, work_dev, work_bytes, infos, st,
+                   [&](int i, SolveProb &P, ProbAux &aux) { return setup_bvp(&probs[i], sps[i], P, aux, st); });
+}
+
+int sc_solve_biharmonic(const sc_bvp *p, void *work_dev, size_t work_bytes, sc_solve_info *info,
+                        sc_stream_t stream) {
+  return sc_solve_biharmonic_batch(p, 1, work_dev, work_bytes, info, stream);
+}
+
+size_t sc_ch_work_bytes(const sc_ch *c) {
+  if (ch_validate(c)) return 0;
+  std::vector<ProbSpec> sps(c->batch);
+  for (int i = 0; i < c->batch; ++i) ch_spec(c, i, nullptr, sps[i]);
+  return batch_bytes(sps);
+}
+
+int sc_ch_step(const sc_ch *c, double *u_dev, void *work_dev, size_t work_bytes, sc_solve_info *infos,
+               sc_stream_t stream) {
+  if (int rc = ch_validate(c)) return rc;
+  if (!u_dev || !infos) return fail(SC_EINVAL, "null pointer");
+  std::vector<ProbSpec> sps(c->batch);
+  for (int i = 0; i < c->batch; ++i) ch_spec(c, i, u_dev, sps[i]);
+  cudaStream_t st = (cudaStream_t)stream;
+  return solve_set(sps, work_dev, work_bytes, infos, st,
+                   [&](int i, SolveProb &P, ProbAux &aux) { return setup_ch(c, sps[i], P, aux, st); });
+}
+
+int sc_ch_stats(const sc_ch *c, const double *u_dev, double *mass_host, double *energy_host, void *work_dev,
+                size_t work_bytes, sc_stream_t stream) {
+  if (int rc = ch_validate(c)) return rc;
+  if (!u_dev || !mass_host || !energy_host || !work_dev) return fail(SC_EINVAL, "null pointer");
+  const long long npts = c->n[0] * c->n[1] * (c->ndim == 3 ? c->n[2] : 1);
+  const int nblk = int((npts + PL_CHUNK - 1) / PL_CHUNK);
+  if (work_bytes < size_t(2 * nblk + 2) * 8) return fail(SC_ENOMEM, "work space too small");
+  double *pm = static_cast<double *>(work_dev), *pe = pm + nblk, *out = pe + nblk;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double h = double(c->h_num) / double(c->h_den);
+  const double hd = c->ndim == 3 ? h * h * h : h * h;
+  for (int b = 0; b < c->batch; ++b) {
+    k_ch_stats_part<<<nblk, PL_NTHR, 0, st>>>(u_dev + (long long)b * npts, c->ndim, int(c->n[0]), int(c->n[1]),
+                                               c->ndim == 3 ? int(c->n[2]) : 1, h, c->kappa, c->chem, c->rho,
+                                               c->ca, c->cb, pm, pe);
+    k_sum_final<<<1, PL_NTHR, 0, st>>>(pm, nblk, out, 0);
+    k_sum_final<<<1, PL_NTHR, 0, st>>>(pe, nblk, out, 1);
+    double hs[2];
+    cudaMemcpyAsync(hs, out, 16, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SC_ECUDA, "stats: %s", cudaGetErrorString(e));
+    mass_host[b] = hs[0];
+    energy_host[b] = hs[1] * hd;
+  }
+  clear_error();
+  return SC_OK;
+}
+
+}  // extern "C"

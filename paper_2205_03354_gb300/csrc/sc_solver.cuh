@@ -1,0 +1,475 @@
+// Persistent batched conjugate-gradient engine.
+//
+// One cooperative launch solves a batch of independent SPD systems
+//     (a I + b B) x = rhs,   B = a composed stencil (Lap o Lap) on a 2D or 3D grid,
+// of uneven sizes.  Every problem owns a contiguous group of CTAs; a group
+// advances its own CG iteration with group barriers (global-memory counters,
+// bounded spins), so small problems never wait for large ones.
+//
+// Per CG iteration (inner precision TI = float or double):
+//   A:  q = (a I + b B) p              tile apply; partial p.q per tile
+//   B:  d += alpha p, rh -= alpha q    chunked vector pass; partial rh.rh
+//   C:  p = rh + beta p                chunked vector pass
+// with a group barrier after each phase.  Reductions are deterministic: every
+// tile/chunk writes its partial to a fixed slot and the last CTA to arrive at
+// the barrier sums the slots in index order, so a problem's result does not
+// depend on its group size or on the rest of the batch.
+//
+// Mixed precision (TI = float): FP32 stencil applies and vector updates; the
+// FP64 solution x, right-hand side and true residual r = rhs - A x are kept in
+// FP64 and refreshed by reliable updates (Sleijpen & van der Vorst 1996):
+// whenever the FP32 recurrence residual has dropped by the factor `delta`
+// since the last refresh, or meets the tolerance, x += d in FP64, the FP64
+// residual is recomputed with an FP64 apply and becomes the new FP32
+// residual (the search direction is kept).  Convergence is only declared on
+// the FP64 true residual.
+#pragma once
+#include "sc_apply.cuh"
+
+namespace sc {
+
+enum { ST_RUNNING = 0, ST_DONE = 1 };
+
+struct SolveState {
+  long long iters;   // inner iterations so far
+  long long outer;   // reliable updates (FP64 residual refreshes)
+  double rr;         // current recurrence residual^2 (inner precision)
+  double rmax;       // |rh| at the last refresh (mixed)
+  double bnorm;      // |rhs|_2
+  double rel;        // last true relative residual
+  double sumb;       // sum(rhs) (mean fix)
+  int status;        // SC_OK while running / final status
+  int phase;         // 0 = not started, 1 = iterating, 2 = finished
+  double beta;       // pending beta for phase C
+};
+
+struct SolveProb {
+  int ndim, nx, ny, nz, bc;
+  long long npts;
+  int H_in, H_64;            // planes per apply tile (inner, FP64 tile shapes)
+  int ntiles_in, ntiles_64;  // tile counts
+  int nchunks;               // vector-phase chunks
+  int nslot;                 // partial slots per reduction value
+  int cta0, ncta;            // CTA group
+  double a, b;               // operator a I + b B
+  int mixed, mean_fix;
+  int vec_in, vec_64;        // 16-byte tile loads legal (alignment checked on host)
+  double rtol, delta;
+  long long maxit;
+  const double *w64;         // dense weight box of B (FP64)
+  const void *wT;            // the same in the inner type
+  double *x, *rhs, *r;       // FP64 vectors
+  void *rh, *p, *q, *d;      // inner vectors (FP64 path: rh == r, d == x)
+  double *part;              // 3 * nslot partial sums
+  double *scal;              // 4 published scalars
+  unsigned *bar;             // [0] arrival counter, [1] release generation
+  SolveState *st;
+};
+
+constexpr int CG_NTHR = 128;
+constexpr int CG_CHUNK = CG_NTHR * 32;  // elements per vector-phase chunk
+constexpr long long SPIN_LIMIT = 1LL << 24;  // ~1-2 s with the back-off below
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Group barrier that also reduces `nval` partial arrays (part[k*nslot + i],
+// i < nused) in index order; the sums are returned in out[0..nval-1] in every
+// CTA of the group.  Returns false when a wait timed out (the problem is then
+// marked SC_ETIMEOUT and every CTA of the group leaves).
+struct GroupCtx {
+  const SolveProb *P;
+  int rank;
+  unsigned target;  // arrival count to wait for
+  unsigned gen;     // release generation
+  double *red;      // shared scratch (>= CG_NTHR/32 doubles)
+  int *flag;        // shared int
+};
+
+__device__ __forceinline__ double fixed_sum(const double *a, int n, double *red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += CG_NTHR) s += __ldcg(a + i);
+  return block_sum<CG_NTHR>(s, red);
+}
+
+__device__ bool group_reduce(GroupCtx &G, int nval, int nused, double *out) {
+  const SolveProb &P = *G.P;
+  __shared__ double s_out[4];
+  __syncthreads();
+  bool ok = true;
+  if (P.ncta == 1) {
+    for (int k = 0; k < nval; ++k) {
+      __threadfence_block();
+      double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
+      if (threadIdx.x == 0) s_out[k] = v;
+    }
+    __syncthreads();
+  } else {
+    G.target += P.ncta;
+    G.gen += 1;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned old = atomicAdd(&P.bar[0], 1u);
+      *G.flag = (old == G.target - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*G.flag) {  // last to arrive: reduce in fixed order and publish
+      __threadfence();
+      for (int k = 0; k < nval; ++k) {
+        double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
+        if (threadIdx.x == 0) P.scal[k] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&P.bar[1], G.gen);
+      }
+    } else if (threadIdx.x == 0) {
+      long long spins = 0;
+      while (ld_acquire(&P.bar[1]) < G.gen) {
+        if (++spins > SPIN_LIMIT) {
+          *G.flag = -1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __syncthreads();
+    if (*G.flag == -1) {
+      ok = false;
+      if (threadIdx.x == 0) {
+        P.st->status = SC_ETIMEOUT;
+        P.st->phase = 2;
+      }
+    }
+    if (threadIdx.x == 0 && ok) {
+      __threadfence();
+      for (int k = 0; k < nval; ++k) s_out[k] = __ldcg(P.scal + k);
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < nval; ++k) out[k] = s_out[k];
+  __syncthreads();
+  return ok;
+}
+
+template <typename T, int NDIM, int R>
+struct WBox {
+  T w[BoxWeights<T, NDIM, R>::N];
+};
+
+// Epilogue of the CG apply: q = a p + b (B p), partial p.q.
+template <typename T, int NDIM, int VX>
+struct CgApplyEpi {
+  const T *__restrict__ p;
+  T *__restrict__ q;
+  long long sy, ss;
+  int nx;
+  double a, b, dot;
+  __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX]) {
+    const long long base = (long long)j * (NDIM == 3 ? ss : sy) + (NDIM == 3 ? (long long)yy * sy : 0);
+#pragma unroll
+    for (int vx = 0; vx < VX; ++vx) {
+      if (xo + vx < nx) {
+        const long long i = base + xo + vx;
+        const T pv = __ldcg(p + i);
+        const T qv = T(a) * pv + T(b) * v[vx];
+        q[i] = qv;
+        dot += double(pv) * double(qv);
+      }
+    }
+  }
+};
+
+// Epilogue of the FP64 residual: r = rhs - (a x + b (B x)), partial r.r.
+template <int NDIM, int VX>
+struct ResidEpi {
+  const double *__restrict__ x;
+  const double *__restrict__ rhs;
+  double *__restrict__ r;
+  long long sy, ss;
+  int nx;
+  double a, b, dot;
+  __device__ __forceinline__ void operator()(int j, int yy, int xo, const double (&v)[VX]) {
+    const long long base = (long long)j * (NDIM == 3 ? ss : sy) + (NDIM == 3 ? (long long)yy * sy : 0);
+#pragma unroll
+    for (int vx = 0; vx < VX; ++vx) {
+      if (xo + vx < nx) {
+        const long long i = base + xo + vx;
+        const double rv = __ldcg(rhs + i) - fma(b, v[vx], a * __ldcg(x + i));
+        r[i] = rv;
+        dot += rv * rv;
+      }
+    }
+  }
+};
+
+template <typename T, int NDIM, int R>
+__device__ __forceinline__ ApplyGeom cg_geom(const SolveProb &P, int H) {
+  ApplyGeom g;
+  g.nx = P.nx;
+  g.ny = P.ny;
+  g.nz = NDIM == 3 ? P.nz : 1;
+  g.bc = P.bc;
+  g.H = H;
+  g.vec = sizeof(T) == 8 ? P.vec_64 : P.vec_in;
+  g.in_sy = P.nx;
+  g.in_ss = (long long)P.nx * P.ny;
+  g.out_sy = P.nx;
+  g.out_ss = (long long)P.nx * P.ny;
+  return g;
+}
+
+template <typename K>
+__device__ __forceinline__ void tile_origin(const SolveProb &P, int tile, int H, int ndim, int &x0,
+                                            int &y0, int &z0) {
+  const int tx = (P.nx + K::BX - 1) / K::BX;
+  if (ndim == 3) {
+    const int ty = (P.ny + K::BY - 1) / K::BY;
+    x0 = (tile % tx) * K::BX;
+    y0 = ((tile / tx) % ty) * K::BY;
+    z0 = (tile / (tx * ty)) * H;
+  } else {
+    x0 = (tile % tx) * K::BX;
+    y0 = 0;
+    z0 = (tile / tx) * H;
+  }
+}
+
+// Phase A: q = A p over the group's tiles.
+template <typename T, int NDIM, int R>
+__device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, double *red) {
+  using K = FlatApply<T, NDIM, R, CLS_CROSS2>;
+  const ApplyGeom g = cg_geom<T, NDIM, R>(P, P.H_in);
+  const WBox<T, NDIM, R> W = *reinterpret_cast<const WBox<T, NDIM, R> *>(P.wT);
+  for (int tile = rank; tile < P.ntiles_in; tile += P.ncta) {
+    int x0, y0, z0;
+    tile_origin<K>(P, tile, P.H_in, NDIM, x0, y0, z0);
+    CgApplyEpi<T, NDIM, K::VX> epi{static_cast<const T *>(P.p), static_cast<T *>(P.q), g.out_sy,
+                                   g.out_ss, P.nx, P.a, P.b, 0.0};
+    K::run_tile(static_cast<const T *>(P.p), g, W, x0, y0, z0, reinterpret_cast<T *>(smem), epi);
+    const double s = block_sum<CG_NTHR>(epi.dot, red);
+    if (threadIdx.x == 0) P.part[tile] = s;
+  }
+}
+
+// FP64 residual r = rhs - A x over the FP64 tiles; partial r.r in slot 0 and
+// (when mean_fix) partial sum(x) in slot 1.
+template <int NDIM, int R>
+__device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, double *red) {
+  using K = FlatApply<double, NDIM, R, CLS_CROSS2>;
+  const ApplyGeom g = cg_geom<double, NDIM, R>(P, P.H_64);
+  const WBox<double, NDIM, R> W = *reinterpret_cast<const WBox<double, NDIM, R> *>(P.w64);
+  for (int tile = rank; tile < P.ntiles_64; tile += P.ncta) {
+    int x0, y0, z0;
+    tile_origin<K>(P, tile, P.H_64, NDIM, x0, y0, z0);
+    ResidEpi<NDIM, K::VX> epi{P.x, P.rhs, P.r, g.out_sy, g.out_ss, P.nx, P.a, P.b, 0.0};
+    K::run_tile(P.x, g, W, x0, y0, z0, reinterpret_cast<double *>(smem), epi);
+    const double s = block_sum<CG_NTHR>(epi.dot, red);
+    if (threadIdx.x == 0) P.part[tile] = s;
+  }
+}
+
+// Vector phases over fixed chunks.  kind:
+//  0: init     rh = TI(r), p = rh, d = 0 (mixed); partials rh.rh, rhs.rhs, sum(rhs)
+//  1: update   d += alpha p, rh -= alpha q; partial rh.rh
+//  2: direction p = rh + beta p
+//  3: refresh  x += d, d = 0 (mixed)
+//  4: to-inner rh = TI(r); partial rh.rh
+//  5: sum(x)   partial
+//  6: shift    x += c
+template <typename TI>
+__device__ void phase_vec(const SolveProb &P, int rank, int kind, double s1, double *red) {
+  TI *rh = static_cast<TI *>(P.rh), *p = static_cast<TI *>(P.p), *q = static_cast<TI *>(P.q),
+     *d = static_cast<TI *>(P.d);
+  for (int c = rank; c < P.nchunks; c += P.ncta) {
+    const long long e0 = (long long)c * CG_CHUNK;
+    const long long e1 = min(e0 + CG_CHUNK, P.npts);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (long long i = e0 + threadIdx.x; i < e1; i += CG_NTHR) {
+      switch (kind) {
+        case 0: {
+          const TI v = TI(__ldcg(P.r + i));
+          rh[i] = v;
+          p[i] = v;
+          if (P.mixed) d[i] = TI(0);
+          a0 += double(v) * double(v);
+          const double bv = __ldcg(P.rhs + i);
+          a1 += bv * bv;
+          a2 += bv;
+          break;
+        }
+        case 1: {
+          const TI al = TI(s1);
+          const TI pv = __ldcg(p + i);
+          d[i] = __ldcg(d + i) + al * pv;
+          const TI v = __ldcg(rh + i) - al * __ldcg(q + i);
+          rh[i] = v;
+          a0 += double(v) * double(v);
+          break;
+        }
+        case 2:
+          p[i] = __ldcg(rh + i) + TI(s1) * __ldcg(p + i);
+          break;
+        case 3:
+          P.x[i] = __ldcg(P.x + i) + double(__ldcg(d + i));
+          d[i] = TI(0);
+          break;
+        case 4: {
+          const TI v = TI(__ldcg(P.r + i));
+          rh[i] = v;
+          a0 += double(v) * double(v);
+          break;
+        }
+        case 5:
+          a0 += __ldcg(P.x + i);
+          break;
+        case 6:
+          P.x[i] = __ldcg(P.x + i) + s1;
+          break;
+      }
+    }
+    if (kind == 0 || kind == 1 || kind == 4 || kind == 5) {
+      const double t0 = block_sum<CG_NTHR>(a0, red);
+      if (threadIdx.x == 0) P.part[c] = t0;
+      if (kind == 0) {
+        const double t1 = block_sum<CG_NTHR>(a1, red);
+        if (threadIdx.x == 0) P.part[P.nslot + c] = t1;
+        const double t2 = block_sum<CG_NTHR>(a2, red);
+        if (threadIdx.x == 0) P.part[2 * P.nslot + c] = t2;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
+
+// Runs one problem for at most `budget` inner iterations.
+template <typename TI, int NDIM, int R>
+__device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget) {
+  const SolveProb &P = *G.P;
+  SolveState &S = *P.st;
+  double red_out[4];
+  double *red = G.red;
+  // scalars live in registers, identical in every CTA of the group
+  long long iters = S.iters, outer = S.outer;
+  double rr = S.rr, rmax = S.rmax, bnorm = S.bnorm, rel = S.rel, sumb = S.sumb, beta = S.beta;
+  int phase = S.phase;
+  int status = SC_OK;
+  const double tol = P.rtol;
+
+  if (phase == 0) {
+    // r = rhs - A x0 (FP64); rh = r; p = rh
+    phase_resid<NDIM, R>(P, G.rank, smem, red);
+    if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
+    phase_vec<TI>(P, G.rank, 0, 0.0, red);
+    if (!group_reduce(G, 3, P.nchunks, red_out)) return;
+    rr = red_out[0];
+    bnorm = sqrt(red_out[1]);
+    sumb = red_out[2];
+    rmax = sqrt(rr);
+    rel = bnorm > 0 ? sqrt(rr) / bnorm : 0.0;
+    beta = 0.0;
+    phase = 1;
+    if (bnorm == 0.0 || sqrt(rr) <= tol * bnorm) phase = 3;  // already converged
+  }
+
+  long long done = 0;
+  while (phase == 1 && done < budget) {
+    if (iters >= P.maxit) {
+      status = SC_ENOTCONV;
+      phase = 3;
+      break;
+    }
+    // A: q = A p, p.q
+    phase_apply<TI, NDIM, R>(P, G.rank, smem, red);
+    if (!group_reduce(G, 1, P.ntiles_in, red_out)) return;
+    const double pq = red_out[0];
+    if (!finite_pos(pq) || !(rr == rr)) {
+      status = SC_EBREAKDOWN;
+      phase = 3;
+      break;
+    }
+    const double alpha = rr / pq;
+    // B: d += alpha p, rh -= alpha q, rh.rh
+    phase_vec<TI>(P, G.rank, 1, alpha, red);
+    if (!group_reduce(G, 1, P.nchunks, red_out)) return;
+    double rr_new = red_out[0];
+    ++iters;
+    ++done;
+    const double rn = sqrt(rr_new);
+    if (!(rn == rn)) {
+      status = SC_EBREAKDOWN;
+      phase = 3;
+      break;
+    }
+    if (P.mixed) {
+      if (rn <= P.delta * rmax || rn <= tol * bnorm) {
+        // reliable update: x += d in FP64, true residual, new rh
+        phase_vec<TI>(P, G.rank, 3, 0.0, red);
+        if (!group_reduce(G, 0, 0, red_out)) return;
+        phase_resid<NDIM, R>(P, G.rank, smem, red);
+        if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
+        ++outer;
+        rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
+        if (rel <= tol) {
+          phase = 3;
+          break;
+        }
+        phase_vec<TI>(P, G.rank, 4, 0.0, red);
+        if (!group_reduce(G, 1, P.nchunks, red_out)) return;
+        rr_new = red_out[0];
+        rmax = sqrt(rr_new);
+      }
+    } else if (rn <= tol * bnorm) {
+      phase = 3;  // FP64 recurrence residual met the tolerance
+      break;
+    }
+    beta = rr_new / rr;
+    rr = rr_new;
+    // C: p = rh + beta p
+    phase_vec<TI>(P, G.rank, 2, beta, red);
+    if (!group_reduce(G, 0, 0, red_out)) return;
+  }
+
+  if (phase == 3) {
+    // finish: FP64 x (mixed: fold d), optional mean fix, true residual
+    if (P.mixed) {
+      phase_vec<TI>(P, G.rank, 3, 0.0, red);
+      if (!group_reduce(G, 0, 0, red_out)) return;
+    }
+    if (P.mean_fix) {
+      phase_vec<TI>(P, G.rank, 5, 0.0, red);
+      if (!group_reduce(G, 1, P.nchunks, red_out)) return;
+      const double c = (sumb - red_out[0]) / double(P.npts);
+      phase_vec<TI>(P, G.rank, 6, c, red);
+      if (!group_reduce(G, 0, 0, red_out)) return;
+    }
+    phase_resid<NDIM, R>(P, G.rank, smem, red);
+    if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
+    rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
+    if (status == SC_OK && !(rel <= tol)) {
+      // the recurrence met the tolerance but the true residual did not:
+      // report it honestly
+      status = (rel == rel) ? SC_ENOTCONV : SC_EBREAKDOWN;
+    }
+    phase = 2;
+  }
+  if (G.rank == 0 && threadIdx.x == 0) {
+    S.iters = iters;
+    S.outer = outer;
+    S.rr = rr;
+    S.rmax = rmax;
+    S.bnorm = bnorm;
+    S.rel = rel;
+    S.sumb = sumb;
+    S.beta = beta;
+    S.phase = phase;
+    if (phase == 2) S.status = status;
+  }
+}
+
+}  // namespace sc

@@ -1,0 +1,174 @@
+"""GPU solves (plate problem, Cahn-Hilliard steps, batches) against the oracle.
+
+Every solve must reach a TRUE relative residual ||b - A x|| / ||b|| <= rtol
+(recomputed in FP64 by the library).  The error of each result against the
+FP64 oracle solution of the same discrete problem is bounded by
+kappa * (rtol + oracle residual), kappa the closed-form condition number;
+the measured error is printed with each result.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.libutil import ensure_built  # noqa: E402
+
+ensure_built()
+import paper_2205_03354_gb300 as sc  # noqa: E402
+from oracle import bvp as obvp  # noqa: E402
+from oracle import ch as och  # noqa: E402
+from oracle import stencil as ost  # noqa: E402
+from synth_inputs import manufactured  # noqa: E402
+
+DEV = "cuda:0"
+RTOL = 1e-10
+
+
+def kappa_bvp(n, ndim):
+    h = 1.0 / (n + 1)
+    return (4.0 * ndim / h**2 / (ndim * np.pi**2)) ** 2
+
+
+def bvp_inputs(n, ndim, ks=None):
+    m = manufactured.bvp_case(n, ndim, 2, ks)
+    f = torch.from_numpy(m["g"]).to(DEV)
+    g = torch.from_numpy(m["u_padded"]).to(DEV)
+    x = torch.full(m["u_exact"].shape, np.nan, dtype=torch.float64, device=DEV)
+    return m, f, g, x
+
+
+def oracle_bvp(m, n, ndim):
+    w = ost.fp_weights(ost.bilaplacian(ndim, 2), Fraction(1, n + 1), np.float64)
+    return obvp.solve_direct(w, m["g"], m["u_padded"], 2)
+
+
+@pytest.mark.parametrize("n,ndim,prec,solver", [
+    (16, 2, "f64", "persistent"), (32, 2, "f64", "persistent"), (64, 2, "f64", "persistent"),
+    (64, 2, "f64", "plain"), (16, 2, "mixed", "persistent"), (33, 2, "mixed", "persistent"),
+    (31, 2, "f64", "persistent"), (12, 3, "f64", "persistent"), (12, 3, "mixed", "persistent"),
+    (17, 3, "f64", "plain"),
+])
+def test_bvp_matches_oracle(n, ndim, prec, solver):
+    m, f, g, x = bvp_inputs(n, ndim)
+    info = sc.solve_biharmonic(f, g, x, prec=prec, solver=solver, rtol=RTOL)
+    assert info["status"] == 0, info
+    assert info["rel_res"] <= RTOL, info
+    assert info["prec"] == prec
+    xs = x.cpu().numpy()
+    ref = oracle_bvp(m, n, ndim)
+    err = np.linalg.norm(xs - ref) / np.linalg.norm(ref)
+    print(f"N={n} {ndim}D {prec} {solver}: iters {info['iters']} outer {info['outer']} "
+          f"relres {info['rel_res']:.2e} err vs oracle {err:.2e}")
+    assert err <= 2 * kappa_bvp(n, ndim) * RTOL
+    # same discretisation error against the exact solution as the oracle
+    e_gpu = np.max(np.abs(xs - m["u_exact"]))
+    e_ref = np.max(np.abs(ref - m["u_exact"]))
+    assert abs(e_gpu - e_ref) <= 1e-3 * e_ref + 2 * kappa_bvp(n, ndim) * RTOL * np.max(np.abs(ref))
+
+
+def test_bvp_second_order_convergence():
+    """Sec. 3.3: second-order convergence of the composed 13-point solve."""
+    errs = []
+    for n in (16, 32, 64):
+        m, f, g, x = bvp_inputs(n, 2)
+        info = sc.solve_biharmonic(f, g, x, prec="f64", rtol=RTOL)
+        assert info["status"] == 0
+        errs.append(float(np.max(np.abs(x.cpu().numpy() - m["u_exact"]))))
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.9 < r < 2.2 for r in rates), (errs, rates)
+
+
+def test_batch_equals_alone():
+    """Uneven 2D/3D plate problems in one batched persistent launch give the
+    same bits as each problem solved alone."""
+    specs = [(24, 2, "f64"), (40, 2, "mixed"), (12, 3, "f64"), (17, 2, "f64"), (10, 3, "mixed"),
+             (57, 2, "f64")]
+    alone, probs, xs, keep = [], [], [], []
+    for n, nd, prec in specs:
+        m, f, g, x = bvp_inputs(n, nd, ks=(1, 2, 1)[:nd])
+        info = sc.solve_biharmonic(f, g, x, prec=prec, rtol=RTOL)
+        assert info["status"] == 0 and info["rel_res"] <= RTOL
+        alone.append(x.clone())
+        x2 = torch.full_like(x, np.nan)
+        probs.append(sc.make_bvp(f, g, x2, prec=prec, rtol=RTOL))
+        xs.append(x2)
+        keep.append((f, g))
+    infos = sc.solve_biharmonic_batch(probs)
+    for a, b, info in zip(alone, xs, infos):
+        assert info["status"] == 0 and info["rel_res"] <= RTOL
+        assert torch.equal(a, b)
+
+
+def test_iteration_cap_reports_not_converged():
+    m, f, g, x = bvp_inputs(32, 2)
+    with pytest.raises(sc.ScError):
+        sc.solve_biharmonic(f, g, x, rtol=-1.0)
+    info = sc.solve_biharmonic(f, g, x, prec="f64", rtol=RTOL, maxit=3)
+    assert info["status"] == 3 and info["iters"] == 3  # SC_ENOTCONV
+    info = sc.solve_biharmonic(f, g, x, prec="f64", solver="plain", rtol=RTOL, maxit=3)
+    assert info["status"] == 3
+
+
+@pytest.mark.parametrize("ndim,n,batch,eps,dt,prec", [
+    (2, 128, 1, 0.01, 1e-6, "auto"), (2, 64, 1, 0.05, 5e-5, "f64"), (2, 96, 2, 0.05, 5e-5, "mixed"),
+    (3, 32, 2, 0.02, 1e-6, "auto"), (3, 20, 1, 0.1, 1e-4, "mixed"),
+])
+def test_ch_step_matches_oracle(ndim, n, batch, eps, dt, prec):
+    shape = (n,) * ndim
+    u0 = manufactured.ch_uniform(n, ndim, seed=21, amp=0.05, batch=batch)
+    u = torch.from_numpy(u0.copy()).to(DEV)
+    c = sc.make_ch(shape, batch, (1, n), dt, 1.0, eps * eps, prec=prec, rtol=RTOL)
+    infos = sc.ch_step(c, u)
+    got = u.cpu().numpy()
+    for b in range(batch):
+        info = infos[b]
+        assert info["status"] == 0 and info["rel_res"] <= RTOL, info
+        ref = och.step_fft(u0[b], 1.0 / n, dt, 1.0, eps * eps, ("cubic",))
+        err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+        kap = 1 + dt * eps * eps * (4 * ndim * n * n) ** 2
+        print(f"CH {ndim}D n={n} b={b} {info['prec']}: iters {info['iters']} relres {info['rel_res']:.2e} "
+              f"err vs oracle {err:.2e}")
+        assert err <= 2 * kap * RTOL + 1e-13
+        # mass: the periodic operator conserves the mean
+        assert abs(got[b].sum() - u0[b].sum()) <= 1e-12 * np.abs(u0[b]).sum()
+
+
+def test_ch_plain_matches_persistent():
+    n = 64
+    u0 = manufactured.ch_uniform(n, 2, seed=5, amp=0.3)
+    c1 = sc.make_ch((n, n), 1, (1, n), 2e-5, 1.0, 0.05**2, prec="f64", rtol=1e-12)
+    c2 = sc.make_ch((n, n), 1, (1, n), 2e-5, 1.0, 0.05**2, prec="f64", solver="plain", rtol=1e-12)
+    u1 = torch.from_numpy(u0.copy()).to(DEV)
+    u2 = torch.from_numpy(u0.copy()).to(DEV)
+    i1 = sc.ch_step(c1, u1)[0]
+    i2 = sc.ch_step(c2, u2)[0]
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert torch.allclose(u1, u2, rtol=0, atol=1e-11)
+
+
+def test_ch_stats_match_oracle():
+    n = 48
+    u0 = manufactured.ch_uniform(n, 2, seed=8, amp=0.5, batch=2)
+    c = sc.make_ch((n, n), 2, (1, n), 1e-6, 1.0, 0.02**2)
+    m, e = sc.ch_stats(c, torch.from_numpy(u0).to(DEV))
+    for b in range(2):
+        assert abs(m[b] - och.mass(u0[b])) <= 1e-12 * np.abs(u0[b]).sum()
+        ref = och.free_energy(u0[b], 1.0 / n, 0.02**2, ("cubic",))
+        assert abs(e[b] - ref) <= 1e-12 * abs(ref)
+
+
+def test_ch_double_well_matches_oracle():
+    """The spinodal benchmark's free energy (Sec. 4.1): rho 5, ca 0.3, cb 0.7,
+    kappa 2, M 5 on 64^2 with h = 200/64, dt 0.05."""
+    n, L = 64, 200
+    u0 = manufactured.ch_spinodal_ic(n, 2, float(L))
+    u = torch.from_numpy(u0.copy()).to(DEV)
+    c = sc.make_ch((n, n), 1, (L, n), 0.05, 5.0, 2.0, chem="double_well", rho=5.0, ca=0.3, cb=0.7,
+                   prec="auto", rtol=RTOL)
+    info = sc.ch_step(c, u)[0]
+    assert info["status"] == 0 and info["rel_res"] <= RTOL
+    ref = och.step_fft(u0, L / n, 0.05, 5.0, 2.0, ("double_well", 5.0, 0.3, 0.7))
+    assert np.max(np.abs(u.cpu().numpy() - ref)) <= 1e-9
