@@ -251,6 +251,22 @@ int sc_ch_step(const sc_ch *p, double *u_dev, void *work_dev, size_t work_bytes,
 int sc_ch_stats(const sc_ch *p, const double *u_dev, double *mass_host, double *energy_host,
                 void *work_dev, size_t work_bytes, sc_stream_t stream);
 
+
+/* Same statistics as sc_ch_stats without any work buffer, for callers that
+ * cannot allocate device memory (a host program whose own pool allocator
+ * owns all device memory, or a latency-critical loop where cudaMalloc, which
+ * may synchronise the device, is not allowed).  The paper has no counterpart:
+ * this is a deployment convenience.  The partial sums live in a fixed array
+ * of 2 * 4096 + 8 doubles inside the library, resident on each GPU that uses
+ * it until the process exits; fields of more than 2^24 grid points are
+ * rejected with SC_EINVAL.  The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress) with that device current and
+ * should happen outside any stream capture.  All calls share the array:
+ * calls that may overlap on the GPU (other streams or host threads) race and
+ * must be serialised by the caller.  Allocates nothing. */
+int sc_ch_stats_noalloc(const sc_ch *p, const double *u_dev, double *mass_host, double *energy_host,
+                        sc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

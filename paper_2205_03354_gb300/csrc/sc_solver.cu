@@ -14,6 +14,7 @@
 #include "sc_internal.h"
 #include "sc_solver.cuh"
 #include "sc_solver_host.h"
+#include "sc_stats_kernels.h"
 
 namespace sc {
 
@@ -79,6 +80,7 @@ __global__ void k_fprime(const double *__restrict__ u, double *__restrict__ g, l
 // ---- plain CG helpers (one kernel per operation) --------------------------
 constexpr int PL_NTHR = 256;
 constexpr int PL_CHUNK = PL_NTHR * 16;
+static_assert(PL_NTHR == STATS_NTHR && PL_CHUNK == STATS_CHUNK, "statistics kernel shape");
 
 __global__ void k_dot_part(const double *__restrict__ a, const double *__restrict__ b, long long n,
                            double *__restrict__ part) {

@@ -166,3 +166,17 @@ def ch_stats(c: Ch, u: torch.Tensor, work=None, stream=None):
     check(lib.sc_ch_stats(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), m, e, ctypes.c_void_p(w.data_ptr()),
                           nb, stream_arg(stream)))
     return list(m), list(e)
+
+
+lib.sc_ch_stats_noalloc.argtypes = [_CP, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+lib.sc_ch_stats_noalloc.restype = ctypes.c_int
+
+
+def ch_stats_noalloc(c: Ch, u: torch.Tensor, stream=None):
+    """sc_ch_stats without a work buffer (fixed library scratch, at most 2^24
+    grid points per field; calls sharing a device must not overlap)."""
+    m = (ctypes.c_double * c.batch)()
+    e = (ctypes.c_double * c.batch)()
+    check(lib.sc_ch_stats_noalloc(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), m, e, stream_arg(stream)))
+    return list(m), list(e)
