@@ -38,7 +38,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="apply_sweep", choices=["apply_sweep"])
+    ap.add_argument("--workload", default="apply_sweep",
+                    choices=["apply_sweep", "bvp", "ch2d", "ch3d", "serving"])
+    ap.add_argument("--nreq", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--n2d", default="32,256", help="serving: 2D interior size range (log-uniform)")
+    ap.add_argument("--n3d", default="16,40", help="serving: 3D interior size range (log-uniform)")
+    ap.add_argument("--load", type=float, default=0.7, help="serving: offered load vs plain-path capacity")
+    ap.add_argument("--slice-ms", type=float, default=2.0)
+    ap.add_argument("--n", type=int, default=0, help="grid size override for solver workloads")
+    ap.add_argument("--solver", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "f64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -276,6 +285,190 @@ def run_apply_sweep_oracle(budget_s: float = 20.0):
 
 
 # ---------------------------------------------------------------------------
+# solver workloads
+# ---------------------------------------------------------------------------
+
+def run_bvp(args, local):
+    """Plate problem of Sec. 3.3 on an N x N interior grid (default 64):
+    time per solve to a true relative residual of 1e-10."""
+    import numpy as np
+    import torch
+    import paper_2205_03354_gb300 as sc
+    from synth_inputs import manufactured
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    n = args.n or 64
+    m = manufactured.bvp_case(n, 2, 2)
+    f = torch.from_numpy(m["g"]).to(dev)
+    g = torch.from_numpy(m["u_padded"]).to(dev)
+    x = torch.empty((n, n), dtype=torch.float64, device=dev)
+    b = sc.make_bvp(f, g, x, prec=args.prec, solver=args.solver, rtol=1e-10)
+    work = torch.empty(sc.bvp_work_bytes(b), dtype=torch.uint8, device=dev)
+    infos = []
+    for _ in range(args.warmup):
+        sc.solve_biharmonic(f, g, x, prec=args.prec, solver=args.solver, work=work)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        infos.append(sc.solve_biharmonic(f, g, x, prec=args.prec, solver=args.solver, work=work))
+        t.append(time.perf_counter() - t0)
+    err = float(np.max(np.abs(x.cpu().numpy() - m["u_exact"])))
+    return {"sec": t, "info": infos[-1], "linf_err_vs_exact": err, "n": n}
+
+
+def run_ch(args, local, ndim):
+    """Semi-implicit Cahn-Hilliard steps: 2D 1024^2 (eps 0.01, dt 1e-6) or a
+    batch of 8 3D 256^3 fields (eps 0.02, dt 1e-6), u0 uniform in
+    [-0.05, 0.05] from seeds."""
+    import numpy as np
+    import torch
+    import paper_2205_03354_gb300 as sc
+    from synth_inputs import manufactured
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    if ndim == 2:
+        n, batch, eps = args.n or 1024, 1, 0.01
+    else:
+        n, batch, eps = args.n or 256, 8, 0.02
+    u0 = manufactured.ch_uniform(n, ndim, seed=2205, amp=0.05, batch=batch)
+    u = torch.from_numpy(u0).to(dev)
+    c = sc.make_ch((n,) * ndim, batch, (1, n), 1e-6, 1.0, eps * eps, prec=args.prec, solver=args.solver,
+                   rtol=1e-10)
+    work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
+    m0, e0 = sc.ch_stats(c, u)
+    for _ in range(args.warmup):
+        sc.ch_step(c, u, work=work)
+    torch.cuda.synchronize()
+    t, its = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        infos = sc.ch_step(c, u, work=work)
+        t.append(time.perf_counter() - t0)
+        its.append(max(i["iters"] for i in infos))
+    m1, e1 = sc.ch_stats(c, u)
+    s0 = float(np.abs(u0).sum(axis=tuple(range(1, ndim + 1))).max())
+    return {"sec": t, "iters": its, "info": infos[0], "n": n, "batch": batch,
+            "mass_drift_rel": max(abs(a - b) for a, b in zip(m0, m1)) / s0,
+            "energy": [e0[0], e1[0]]}
+
+
+def run_serving(args, local):
+    """Poisson stream of plate-problem solves of mixed 2D/3D sizes (manufactured
+    u = prod sin(k_a pi x_a), k_a in [1, 8]) to a true relative residual of
+    1e-10.  Plain path: every request alone, FP64 CG one kernel per operation,
+    first come first served, host copies included.  Served path: the same
+    trace replayed in real time through the continuous-batching server (AUTO
+    precision).  The arrival rate is set to `load` times the plain path's
+    measured capacity."""
+    import numpy as np
+    import torch
+    import paper_2205_03354_gb300 as sc
+    from synth_inputs import manufactured, requests
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    lo2, hi2 = (int(v) for v in args.n2d.split(","))
+    lo3, hi3 = (int(v) for v in args.n3d.split(","))
+    tr = requests.trace(args.nreq, seed=2205, rate_per_s=1.0, n2d=(lo2, hi2), n3d=(lo3, hi3))
+    cases = []
+    for q in tr:
+        m = manufactured.bvp_case(q["n"], q["ndim"], 2, q["ks"])
+        cases.append((np.ascontiguousarray(m["g"]), np.ascontiguousarray(m["u_padded"]), m["u_exact"]))
+    # plain path: measure each request alone (copies in and out included)
+    work = None
+    dur, plain_x = [], []
+    for k, (f, g, ue) in enumerate(cases):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ft, gt = torch.from_numpy(f).to(dev), torch.from_numpy(g).to(dev)
+        x = torch.empty(f.shape, dtype=torch.float64, device=dev)
+        info = sc.solve_biharmonic(ft, gt, x, prec="f64", solver="plain", rtol=1e-10)
+        xh = x.cpu().numpy()
+        dur.append(time.perf_counter() - t0)
+        plain_x.append(xh)
+        assert info["status"] == 0, info
+    cap = len(dur) / sum(dur)
+    rate = args.load * cap
+    arr = np.array([q["t"] for q in tr]) / rate  # trace drawn at rate 1
+    end, lat_plain = 0.0, []
+    for a, d in zip(arr, dur):
+        start = max(a, end)
+        end = start + d
+        lat_plain.append(end - a)
+    plain_makespan = end - arr[0]
+    # served path
+    arena = torch.empty(int(min(64 << 30, torch.cuda.mem_get_info(dev)[0] * 0.5)), dtype=torch.uint8, device=dev)
+    srv = sc.Server(arena, max_active=1024, slice_ms=args.slice_ms)
+    xs = [np.full(c[0].shape, np.nan) for c in cases]
+    tickets = [None] * len(cases)
+    results = {}
+    t_start = time.perf_counter()
+    i = 0
+    while len(results) < len(cases):
+        now = time.perf_counter() - t_start
+        while i < len(cases) and arr[i] - arr[0] <= now:
+            f, g, _ = cases[i]
+            tickets[i] = srv.submit(f, g, xs[i], prec="auto", rtol=1e-10)
+            i += 1
+        for k in range(i):
+            if k not in results:
+                r = srv.poll(tickets[k])
+                if r is not None:
+                    results[k] = r
+        time.sleep(0.0002)
+    served_makespan = time.perf_counter() - t_start
+    # saturation: the whole trace submitted at once (capacity of each path)
+    xs2 = [np.full(c[0].shape, np.nan) for c in cases]
+    t0 = time.perf_counter()
+    tk = [srv.submit(c[0], c[1], x2, prec="auto", rtol=1e-10) for c, x2 in zip(cases, xs2)]
+    srv.drain(3600.0)
+    burst = time.perf_counter() - t0
+    for t in tk:
+        srv.poll(t)
+    srv.close()
+    lat_srv = [results[k]["latency_s"] for k in range(len(cases))]
+    ok = all(results[k]["status"] == 0 and results[k]["rel_res"] <= 1e-10 for k in range(len(cases)))
+    errs = [float(np.max(np.abs(xs[k] - plain_x[k])) / max(1e-300, np.max(np.abs(plain_x[k]))))
+            for k in range(len(cases))]
+    pct = lambda v, q: float(np.percentile(np.array(v), q))
+    return {"nreq": len(cases), "rate": rate, "plain_capacity": cap, "all_converged": ok,
+            "plain": {"solves_per_s": len(cases) / plain_makespan, "p50_ms": pct(lat_plain, 50) * 1e3,
+                      "p99_ms": pct(lat_plain, 99) * 1e3, "capacity_solves_per_s": cap},
+            "served": {"solves_per_s": len(cases) / served_makespan, "p50_ms": pct(lat_srv, 50) * 1e3,
+                       "capacity_solves_per_s": len(cases) / burst,
+                       "p99_ms": pct(lat_srv, 99) * 1e3,
+                       "mixed_fraction": sum(results[k]["prec"] == "mixed" for k in results) / len(cases)},
+            "max_rel_diff_vs_plain": max(errs),
+            "sizes": {"2d": [lo2, hi2], "3d": [lo3, hi3]}}
+
+
+def solver_line(args, res, workload):
+    sec = res["sec"]
+    med = statistics.median(sec)
+    if workload == "bvp":
+        value, unit, metric = 1.0 / med, "solves/s", "plate-problem solves/s at true rel. residual 1e-10"
+        cfg = {"workload": f"biharmonic plate BVP, {res['n']}x{res['n']} interior, 13-pt Lap o Lap, "
+                           f"CG to 1e-10, solver {args.solver}, prec {args.prec}"}
+        extra = {"iters": res["info"]["iters"], "outer": res["info"]["outer"], "rel_res": res["info"]["rel_res"],
+                 "prec_used": res["info"]["prec"], "linf_err_vs_exact": res["linf_err_vs_exact"]}
+    else:
+        value, unit = res["batch"] / med, "field-steps/s"
+        metric = "Cahn-Hilliard IMEX steps/s (CG to 1e-10)"
+        nd = 2 if workload == "ch2d" else 3
+        cfg = {"workload": f"{nd}D Cahn-Hilliard, periodic {res['n']}^{nd} x batch {res['batch']}, "
+                           f"solver {args.solver}, prec {args.prec}"}
+        extra = {"iters_per_step": res["iters"], "rel_res": res["info"]["rel_res"], "prec_used": res["info"]["prec"],
+                 "mass_drift_rel": res["mass_drift_rel"], "energy_first_last": res["energy"]}
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": med * 1e3, "ms_p99": sorted(sec)[int(0.99 * (len(sec) - 1))] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else "f64+f32",
+            "data": "synthetic", "config": cfg, "result": extra}
+
+
+# ---------------------------------------------------------------------------
 # distributed helpers
 # ---------------------------------------------------------------------------
 
@@ -363,6 +556,25 @@ def main():
         print(json.dumps(line))
         return 0
 
+    if args.workload == "serving":
+        res = run_serving(args, local)
+        if rank == 0:
+            line = {"metric": "plate-problem solves/s and p50/p99 latency at 1e-10, served vs plain",
+                    "value": res["served"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                    "steps": res["nreq"], "warmup": 0, "ms_per_step": 1e3 / res["served"]["solves_per_s"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+                    "data": "synthetic",
+                    "config": {"workload": f"Poisson stream of {res['nreq']} plate solves, 2D n in "
+                                           f"{res['sizes']['2d']}, 3D n in {res['sizes']['3d']} (log-uniform), "
+                                           f"rate {res['rate']:.2f}/s = {args.load} x plain capacity"},
+                    "result": res}
+            print(json.dumps(line))
+        return 0
+    if args.workload in ("bvp", "ch2d", "ch3d"):
+        res = run_bvp(args, local) if args.workload == "bvp" else run_ch(args, local, 2 if args.workload == "ch2d" else 3)
+        if rank == 0:
+            print(json.dumps(solver_line(args, res, args.workload)))
+        return 0
     init_dist(world, local)
     res = run_apply_sweep_ours(args, rank, world, local)
     tmax = max_over_ranks(res["total_ms"], world)

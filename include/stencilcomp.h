@@ -267,6 +267,69 @@ int sc_ch_stats(const sc_ch *p, const double *u_dev, double *mass_host, double *
 int sc_ch_stats_noalloc(const sc_ch *p, const double *u_dev, double *mass_host, double *energy_host,
                         sc_stream_t stream);
 
+
+/* ---- Serving loop: continuous batching of plate-problem solves ------------- */
+
+/* A server owns one scheduler thread on the device that is current when it is
+ * created.  Requests are queued by sc_submit and admitted, in arrival order
+ * with skipping of requests that do not fit yet, whenever the caller-provided
+ * device arena has room for their fields and Krylov state and fewer than
+ * max_active requests are resident.  Resident requests advance together in
+ * persistent launches of at most slice_ms milliseconds each (every request on
+ * its own group of CTAs); between slices finished requests are retired (their
+ * solution copied to the caller's host buffer, their memory freed) and newly
+ * admitted ones join.  A request's result does not depend on what else is in
+ * flight: it is bit-identical to sc_solve_biharmonic with the same precision.
+ * The server never allocates device memory: everything lives in the arena. */
+typedef struct {
+  void *arena_dev;     /* device memory owned by the caller                   */
+  size_t arena_bytes;  /* its size: the admission budget                     */
+  int32_t max_active;  /* resident requests at most (1..4096)                */
+  double slice_ms;     /* length of one persistent launch (> 0)              */
+} sc_server_cfg;
+
+/* One plate problem (same meaning as sc_bvp), with HOST buffers: f_host and
+ * ghost_host are read at admission, x_host is written when the request
+ * completes; all three must stay valid until sc_poll reports it done. */
+typedef struct {
+  int32_t ndim;
+  int32_t order;
+  int64_t n[3];
+  int32_t prec;
+  double rtol;
+  int64_t maxit;
+  const double *f_host;
+  const double *ghost_host;
+  double *x_host;
+} sc_request;
+
+typedef struct {
+  int32_t status;    /* solve status (SC_OK, SC_ENOTCONV, ...)              */
+  int32_t prec;      /* precision used                                      */
+  int64_t iters;
+  double rel_res;    /* true relative residual                              */
+  double queue_s;    /* submit -> admission                                 */
+  double latency_s;  /* submit -> solution copied to x_host                 */
+} sc_result;
+
+typedef struct sc_server sc_server;
+
+/* Device bytes a request occupies while resident (fields + Krylov state). */
+size_t sc_request_bytes(const sc_request *req);
+int sc_server_create(const sc_server_cfg *cfg, sc_server **out);
+/* Stops the scheduler; requests still queued or resident are abandoned. */
+int sc_server_destroy(sc_server *srv);
+/* Queues a request (never blocks).  SC_EINVAL for a malformed request,
+ * SC_ENOMEM if it could never fit in the arena. */
+int sc_submit(sc_server *srv, const sc_request *req, uint64_t *ticket);
+/* SC_EPENDING while the request is queued or resident; SC_OK once it is
+ * done (x_host written, *out filled; the ticket is then released);
+ * SC_EINVAL for an unknown ticket. */
+int sc_poll(sc_server *srv, uint64_t ticket, sc_result *out);
+/* Waits until nothing is queued or resident, at most timeout_s seconds
+ * (SC_ETIMEOUT otherwise). */
+int sc_server_drain(sc_server *srv, double timeout_s);
+
 #ifdef __cplusplus
 }
 #endif

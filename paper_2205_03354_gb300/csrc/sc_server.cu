@@ -1,0 +1,380 @@
+// Serving loop: continuous batching of plate-problem solves on one GPU.
+//
+// A scheduler thread alternates between (1) admitting queued requests into
+// free space of the caller's device arena (copy fields in, build b = g -
+// A(ring)), (2) one time slice of the persistent CG engine over every
+// resident request, and (3) retiring converged requests (solution to the
+// caller's host buffer, arena space back to the free list).  Requests that
+// arrive while others run join at the next slice boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sc_internal.h"
+#include "sc_solver.cuh"
+#include "sc_solver_host.h"
+
+namespace sc {
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit free list over [0, size).
+class Arena {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+  }
+  bool alloc(size_t bytes, size_t *off) {
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t largest() const {
+    size_t m = 0;
+    for (auto &kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
+
+struct Req {
+  uint64_t id;
+  sc_request rq;
+  ProbSpec sp;
+  size_t bytes = 0, off = 0;
+  SolveProb P;
+  ProbAux aux;
+  double *f = nullptr, *g = nullptr, *x = nullptr;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  bool done = false;
+  sc_result res;
+};
+
+static long long npts_of(const sc_request *r) {
+  long long n = 1;
+  for (int a = 0; a < r->ndim; ++a) n *= r->n[a];
+  return n;
+}
+static long long padded_of(const sc_request *r, int R) {
+  long long n = 1;
+  for (int a = 0; a < r->ndim; ++a) n *= r->n[a] + 2 * R;
+  return n;
+}
+
+// Plate problem view of a request (device pointers filled in at admission).
+static sc_bvp as_bvp(const sc_request *r, const double *f, const double *g, double *x) {
+  sc_bvp b;
+  std::memset(&b, 0, sizeof(b));
+  b.ndim = r->ndim;
+  b.order = r->order;
+  for (int a = 0; a < 3; ++a) b.n[a] = r->n[a];
+  b.prec = r->prec;
+  b.solver = SC_SOLVER_PERSISTENT;
+  b.rtol = r->rtol;
+  b.maxit = r->maxit;
+  b.f_dev = f;
+  b.ghost_dev = g;
+  b.x_dev = x;
+  return b;
+}
+
+static int request_layout(const sc_request *r, ProbSpec &sp, size_t *bytes) {
+  // validation with placeholder pointers (never dereferenced)
+  static double dummy;
+  sc_bvp b = as_bvp(r, &dummy, &dummy, &dummy);
+  if (int rc = bvp_spec(&b, sp)) return rc;
+  Carver cv(nullptr, 0);
+  cv.take(npts_of(r) * 8);                 // f
+  cv.take(padded_of(r, sp.R) * 8);         // ghost field
+  cv.take(npts_of(r) * 8);                 // x
+  SolveProb P;
+  ProbAux aux;
+  layout(sp, cv, P, aux);
+  *bytes = cv.off + 256;
+  return SC_OK;
+}
+
+}  // namespace sc
+
+struct sc_server {
+  sc_server_cfg cfg;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  char *arena_base = nullptr;  // after the descriptor head
+  size_t arena_size = 0;
+  sc::Arena arena;
+  sc::SolveProb *dprobs = nullptr;
+  int *dmap = nullptr;
+  unsigned *dbars = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<sc::Req *> pending;
+  std::vector<sc::Req *> active;
+  std::unordered_map<uint64_t, sc::Req *> all;
+  uint64_t next_id = 1;
+  bool stop = false;
+  int worker_error = 0;
+  std::thread worker;
+};
+
+namespace sc {
+
+static void retire(sc_server *S, Req *r, const SolveState &st) {
+  cudaMemcpy(r->rq.x_host, r->x, npts_of(&r->rq) * 8, cudaMemcpyDeviceToHost);
+  r->t_done = now_s();
+  std::memset(&r->res, 0, sizeof(r->res));
+  r->res.status = st.phase == 2 ? st.status : SC_ETIMEOUT;
+  r->res.prec = r->sp.mixed ? SC_PREC_MIXED : SC_PREC_F64;
+  r->res.iters = st.iters;
+  r->res.rel_res = st.rel;
+  r->res.queue_s = r->t_admit - r->t_submit;
+  r->res.latency_s = r->t_done - r->t_submit;
+}
+
+static void worker_loop(sc_server *S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::vector<Req *> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->active.empty() && S->pending.empty())
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || !S->pending.empty(); });
+      if (S->stop) return;
+      // admit in arrival order, skipping requests that do not fit yet
+      int look = 0;
+      for (auto it = S->pending.begin(); it != S->pending.end() && look < 256;) {
+        ++look;
+        if (int(S->active.size() + admit.size()) >= S->cfg.max_active) break;
+        Req *r = *it;
+        size_t off;
+        if (S->arena.alloc(r->bytes, &off)) {
+          r->off = off;
+          admit.push_back(r);
+          it = S->pending.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    // set up admitted requests (outside the lock)
+    for (Req *r : admit) {
+      Carver cv(S->arena_base + r->off, r->bytes);
+      const long long n = npts_of(&r->rq), np = padded_of(&r->rq, r->sp.R);
+      r->f = static_cast<double *>(cv.take(n * 8));
+      r->g = static_cast<double *>(cv.take(np * 8));
+      r->x = static_cast<double *>(cv.take(n * 8));
+      cudaMemcpyAsync(r->f, r->rq.f_host, n * 8, cudaMemcpyHostToDevice, S->st);
+      cudaMemcpyAsync(r->g, r->rq.ghost_host, np * 8, cudaMemcpyHostToDevice, S->st);
+      r->sp.x = r->x;
+      layout(r->sp, cv, r->P, r->aux);
+      sc_bvp b = as_bvp(&r->rq, r->f, r->g, r->x);
+      int rc = upload_prob(r->sp, r->P, r->aux, S->st);
+      if (!rc) rc = setup_bvp(&b, r->sp, r->P, r->aux, S->st);
+      r->t_admit = now_s();
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (rc) {
+        std::memset(&r->res, 0, sizeof(r->res));
+        r->res.status = rc;
+        r->t_done = now_s();
+        r->res.latency_s = r->t_done - r->t_submit;
+        r->done = true;
+        S->arena.release(r->off, r->bytes);
+        S->cv_done.notify_all();
+      } else {
+        S->active.push_back(r);
+      }
+    }
+    std::vector<Req *> act;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      act = S->active;
+    }
+    if (act.empty()) continue;
+    std::vector<SolveProb> hp(act.size());
+    for (size_t i = 0; i < act.size(); ++i) hp[i] = act[i]->P;
+    int rc = run_persistent(hp, S->dprobs, S->dmap, S->dbars, S->st, LLONG_MAX, S->cfg.slice_ms);
+    std::vector<SolveState> hs(act.size());
+    for (size_t i = 0; i < act.size(); ++i)
+      cudaMemcpyAsync(&hs[i], act[i]->P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, S->st);
+    cudaError_t e = cudaStreamSynchronize(S->st);
+    if (rc || e != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->worker_error = rc ? rc : SC_ECUDA;
+      for (Req *r : act) {
+        std::memset(&r->res, 0, sizeof(r->res));
+        r->res.status = S->worker_error;
+        r->done = true;
+      }
+      S->active.clear();
+      S->cv_done.notify_all();
+      continue;
+    }
+    std::vector<Req *> finished;
+    for (size_t i = 0; i < act.size(); ++i)
+      if (hs[i].phase == 2) {
+        retire(S, act[i], hs[i]);
+        finished.push_back(act[i]);
+      }
+    if (!finished.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (Req *r : finished) {
+        r->done = true;
+        S->arena.release(r->off, r->bytes);
+        S->active.erase(std::find(S->active.begin(), S->active.end(), r));
+      }
+      S->cv_done.notify_all();
+    }
+  }
+}
+
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+size_t sc_request_bytes(const sc_request *req) {
+  if (!req) return 0;
+  ProbSpec sp;
+  size_t b = 0;
+  if (request_layout(req, sp, &b)) return 0;
+  return b;
+}
+
+int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
+  if (!cfg || !out || !cfg->arena_dev) return fail(SC_EINVAL, "null argument");
+  if (cfg->max_active < 1 || cfg->max_active > 4096) return fail(SC_EINVAL, "max_active must be 1..4096");
+  if (!(cfg->slice_ms > 0.0)) return fail(SC_EINVAL, "slice_ms must be positive");
+  const int G = std::max(max_group_ctas(true), max_group_ctas(false));
+  Carver head(nullptr, 0);
+  head.take(size_t(cfg->max_active) * sizeof(SolveProb));
+  head.take(size_t(G) * sizeof(int));
+  head.take(size_t(cfg->max_active) * 2 * sizeof(unsigned));
+  const size_t hbytes = (head.off + 255) & ~size_t(255);
+  if (cfg->arena_bytes <= hbytes + 4096) return fail(SC_ENOMEM, "arena smaller than the server's descriptors");
+  sc_server *S = new sc_server();
+  S->cfg = *cfg;
+  cudaGetDevice(&S->device);
+  if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete S;
+    return fail(SC_ECUDA, "stream creation failed");
+  }
+  Carver hc(cfg->arena_dev, cfg->arena_bytes);
+  S->dprobs = static_cast<SolveProb *>(hc.take(size_t(cfg->max_active) * sizeof(SolveProb)));
+  S->dmap = static_cast<int *>(hc.take(size_t(G) * sizeof(int)));
+  S->dbars = static_cast<unsigned *>(hc.take(size_t(cfg->max_active) * 2 * sizeof(unsigned)));
+  S->arena_base = static_cast<char *>(cfg->arena_dev) + hbytes;
+  S->arena_size = cfg->arena_bytes - hbytes;
+  S->arena.reset(S->arena_size);
+  S->worker = std::thread(worker_loop, S);
+  *out = S;
+  clear_error();
+  return SC_OK;
+}
+
+int sc_server_destroy(sc_server *S) {
+  if (!S) return fail(SC_EINVAL, "null server");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  cudaStreamSynchronize(S->st);
+  cudaStreamDestroy(S->st);
+  for (auto &kv : S->all) delete kv.second;
+  delete S;
+  clear_error();
+  return SC_OK;
+}
+
+int sc_submit(sc_server *S, const sc_request *req, uint64_t *ticket) {
+  if (!S || !req || !ticket) return fail(SC_EINVAL, "null argument");
+  if (!req->f_host || !req->ghost_host || !req->x_host) return fail(SC_EINVAL, "null host buffer");
+  Req *r = new Req();
+  r->rq = *req;
+  if (int rc = request_layout(req, r->sp, &r->bytes)) {
+    delete r;
+    return rc;
+  }
+  if (r->bytes > S->arena_size) {
+    delete r;
+    return fail(SC_ENOMEM, "request needs %zu bytes, arena holds %zu", r->bytes, S->arena_size);
+  }
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->id = S->next_id++;
+    S->all[r->id] = r;
+    S->pending.push_back(r);
+    *ticket = r->id;
+  }
+  S->cv_work.notify_all();
+  clear_error();
+  return SC_OK;
+}
+
+int sc_poll(sc_server *S, uint64_t ticket, sc_result *out) {
+  if (!S || !out) return fail(SC_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return fail(SC_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  Req *r = it->second;
+  if (!r->done) return SC_EPENDING;
+  *out = r->res;
+  delete r;
+  S->all.erase(it);
+  clear_error();
+  return SC_OK;
+}
+
+int sc_server_drain(sc_server *S, double timeout_s) {
+  if (!S) return fail(SC_EINVAL, "null server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  const bool ok = S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                      [&] { return S->pending.empty() && S->active.empty(); });
+  if (!ok) return fail(SC_ETIMEOUT, "requests still in flight after %.3f s", timeout_s);
+  clear_error();
+  return SC_OK;
+}
+
+}  // extern "C"

@@ -23,9 +23,9 @@ namespace sc {
 // ---------------------------------------------------------------------------
 
 template <typename TI, int R>
-__global__ void __launch_bounds__(CG_NTHR)
+__global__ void __launch_bounds__(CG_NTHR, 3)
     cg_persistent_kernel(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob,
-                         long long budget) {
+                         long long budget, unsigned long long slice_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[CG_NTHR / 32];
   __shared__ int flag;
@@ -35,9 +35,9 @@ __global__ void __launch_bounds__(CG_NTHR)
   if (P.st->phase == 2) return;
   GroupCtx G{&P, int(blockIdx.x) - P.cta0, 0u, 0u, red, &flag};
   if (P.ndim == 2)
-    cg_run<TI, 2, R>(G, smem, budget);
+    cg_run<TI, 2, R>(G, smem, budget, slice_ns);
   else
-    cg_run<TI, 3, R>(G, smem, budget);
+    cg_run<TI, 3, R>(G, smem, budget, slice_ns);
 }
 
 // out = ring of g (padded array), interior set to zero.
@@ -183,18 +183,7 @@ __global__ void k_ch_stats_part(const double *__restrict__ u, int ndim, int nx, 
 // host side
 // ---------------------------------------------------------------------------
 
-struct Carver {
-  char *base;
-  size_t off = 0, cap;
-  Carver(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
-  void *take(size_t bytes) {
-    off = (off + 255) & ~size_t(255);
-    void *p = base ? base + off : nullptr;
-    off += bytes;
-    return p;
-  }
-  bool ok() const { return base == nullptr || off <= cap; }
-};
+
 
 template <typename T, int NDIM, int R>
 static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
@@ -203,9 +192,12 @@ static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
   const long long txy = ((nx + K::BX - 1) / K::BX) * (NDIM == 3 ? (ny + K::BY - 1) / K::BY : 1);
   const long long planes = NDIM == 3 ? nz : ny;
   const long long npts = nx * ny * nz;
-  const long long target = std::max<long long>(1, npts / 16384);
+  // about one tile per 2048 points, at most ~1024 tiles
+  const long long target = std::max<long long>(1, std::min<long long>(npts / 2048, 1024));
   long long h = (txy * planes + target - 1) / target;
-  h = std::max<long long>(4, std::min<long long>(h, 128));
+  // at least 8 rows (2D) / 4 planes (3D) per tile: the 2R halo rows are
+  // re-read by the neighbouring tile
+  h = std::max<long long>(NDIM == 2 ? 8 : 4, std::min<long long>(h, 128));
   h = std::min<long long>(h, planes);
   H = int(h);
   ntiles = int(txy * ((planes + h - 1) / h));
@@ -221,7 +213,7 @@ static size_t smem_bytes_cg() {
 }
 
 // Lays out one problem's work space; with base == nullptr only sizes.
-static void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
+void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
   std::memset(&P, 0, sizeof(P));
   const long long npts = sp.n[0] * sp.n[1] * (sp.ndim == 3 ? sp.n[2] : 1);
   P.ndim = sp.ndim;
@@ -239,8 +231,12 @@ static void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
     if (!sp.mixed) tiles_for<double, 3, 2>(sp, P.H_in, P.ntiles_in);
     tiles_for<double, 3, 2>(sp, P.H_64, P.ntiles_64);
   }
-  P.nchunks = int((npts + CG_CHUNK - 1) / CG_CHUNK);
-  P.nslot = std::max({P.ntiles_in, P.ntiles_64, P.nchunks});
+  // chunk = CG_STEP * 2^k: the smallest with at most 1024 chunks
+  P.chunk = CG_STEP;
+  while ((npts + P.chunk - 1) / P.chunk > 1024) P.chunk *= 2;
+  P.nchunks = int((npts + P.chunk - 1) / P.chunk);
+  // the plain path reduces in blocks of PL_CHUNK points through the same slots
+  P.nslot = std::max({P.ntiles_in, P.ntiles_64, P.nchunks, int((npts + 4095) / 4096)});
   P.a = sp.a;
   P.b = sp.b;
   P.mixed = sp.mixed;
@@ -279,7 +275,7 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 // Fills the dense weight boxes of B (composed Lap o Lap, exact weights) and
 // the state on the device (asynchronously from pageable host buffers).
-static int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
+int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
   sc_stencil L, B;
   int rc = sc_laplacian(sp.ndim, sp.order, &L);
   if (!rc) rc = sc_compose_stencil(&L, &L, &B);
@@ -314,6 +310,7 @@ static int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cud
   const bool al = aligned16(P.x) && aligned16(P.p) && aligned16(P.r);
   P.vec_in = al && (P.nx % (P.mixed ? 4 : 2) == 0);
   P.vec_64 = al && (P.nx % 2 == 0);
+  P.vec_v = al && aligned16(P.rhs) && aligned16(P.q) && aligned16(P.rh) && aligned16(P.d) && (P.npts % 4 == 0);
   cudaError_t e = cudaStreamSynchronize(st);  // host buffers above are locals
   if (e != cudaSuccess) return fail(SC_ECUDA, "upload: %s", cudaGetErrorString(e));
   return SC_OK;
@@ -322,7 +319,7 @@ static int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cud
 static int grid1d(long long n) { return int(std::min<long long>((n + 255) / 256, 8LL * num_sms())); }
 
 // Right-hand side of the plate problem: rhs = g - A(ring), x = 0.
-static int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
+int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
   const int R = sp.R;
   long long p[3] = {1, 1, 1};
   for (int a = 0; a < sp.ndim; ++a) p[a] = sp.n[a] + 2 * R;
@@ -353,7 +350,8 @@ static int setup_ch(const sc_ch *cp, const ProbSpec &sp, SolveProb &P, const Pro
 // persistent kernel for them.
 template <typename TI>
 static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx, SolveProb *dprobs,
-                        int *dmap, unsigned *dbars, cudaStream_t st, long long budget) {
+                        int *dmap, unsigned *dbars, cudaStream_t st, long long budget,
+                        double slice_ms) {
   auto kern = cg_persistent_kernel<TI, 2>;
   const size_t smem = smem_bytes_cg();
   static bool attr = false;
@@ -396,7 +394,8 @@ static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx,
   const SolveProb *a0 = dprobs;
   const int *a1 = dmap;
   long long a2 = budget;
-  void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2};
+  unsigned long long a3 = slice_ms > 0.0 ? (unsigned long long)(slice_ms * 1e6) : 0ull;
+  void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2, (void *)&a3};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(used), dim3(CG_NTHR), args, smem, st);
   if (e != cudaSuccess) return fail(SC_ECUDA, "cooperative launch: %s", cudaGetErrorString(e));
   // pageable sources above: finish before the vectors go out of scope
@@ -418,7 +417,7 @@ int max_group_ctas(bool mixed) {
 // Runs every problem to completion (waves of at most one CTA per problem
 // beyond the grid size).
 int run_persistent(std::vector<SolveProb> &hp, SolveProb *dprobs, int *dmap, unsigned *dbars,
-                   cudaStream_t st, long long budget) {
+                   cudaStream_t st, long long budget, double slice_ms) {
   for (int mixed = 0; mixed < 2; ++mixed) {
     std::vector<int> all;
     for (size_t i = 0; i < hp.size(); ++i)
@@ -426,8 +425,8 @@ int run_persistent(std::vector<SolveProb> &hp, SolveProb *dprobs, int *dmap, uns
     const int G = max_group_ctas(mixed);
     for (size_t w0 = 0; w0 < all.size(); w0 += size_t(G)) {
       std::vector<int> idx(all.begin() + w0, all.begin() + std::min(all.size(), w0 + size_t(G)));
-      int rc = mixed ? launch_group<float>(hp, idx, dprobs, dmap, dbars, st, budget)
-                     : launch_group<double>(hp, idx, dprobs, dmap, dbars, st, budget);
+      int rc = mixed ? launch_group<float>(hp, idx, dprobs, dmap, dbars, st, budget, slice_ms)
+                     : launch_group<double>(hp, idx, dprobs, dmap, dbars, st, budget, slice_ms);
       if (rc) return rc;
     }
   }
@@ -469,29 +468,48 @@ static int run_plain(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaS
   long long it = 0;
   int status = SC_OK;
   const double tol = sp.rtol;
-  bool conv = std::sqrt(hs[0]) <= tol * std::sqrt(hs[5]);
-  while (!conv) {
-    if (it >= sp.maxit) {
-      status = SC_ENOTCONV;
-      break;
-    }
-    if (int rc = apply_op(p, q)) return rc;
-    dot(p, q, 1);
-    k_alpha<<<1, 1, 0, st>>>(s);
-    k_xr_update<<<g, 256, 0, st>>>(P.x, r, p, q, s, n);
-    dot(r, r, 2);
-    k_beta<<<1, 1, 0, st>>>(s, tol);
-    k_p_update<<<g, 256, 0, st>>>(p, r, s, n);
-    ++it;
-    if ((it & 7) == 0 || it >= sp.maxit) {
-      cudaMemcpyAsync(hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
-      if (hs[7] != 0.0) {
-        status = SC_EBREAKDOWN;
+  const double bn2 = hs[5];
+  bool conv = std::sqrt(hs[0]) <= tol * std::sqrt(bn2);
+  double rel = 0.0;
+  for (;;) {
+    while (!conv) {
+      if (it >= sp.maxit) {
+        status = SC_ENOTCONV;
         break;
       }
-      conv = hs[6] != 0.0;
+      if (int rc = apply_op(p, q)) return rc;
+      dot(p, q, 1);
+      k_alpha<<<1, 1, 0, st>>>(s);
+      k_xr_update<<<g, 256, 0, st>>>(P.x, r, p, q, s, n);
+      dot(r, r, 2);
+      k_beta<<<1, 1, 0, st>>>(s, tol);
+      k_p_update<<<g, 256, 0, st>>>(p, r, s, n);
+      ++it;
+      if ((it & 7) == 0 || it >= sp.maxit) {
+        cudaMemcpyAsync(hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        if (hs[7] != 0.0) {
+          status = SC_EBREAKDOWN;
+          break;
+        }
+        conv = hs[6] != 0.0;
+      }
     }
+    if (status != SC_OK) break;
+    // the recurrence met the tolerance: check the true residual
+    if (int rc = apply_op(P.x, r)) return rc;
+    k_sub_from<<<g, 256, 0, st>>>(r, P.rhs, n);
+    dot(r, r, 0);
+    cudaMemcpyAsync(hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    rel = bn2 > 0 ? std::sqrt(hs[0]) / std::sqrt(bn2) : 0.0;
+    if (rel <= tol || it >= sp.maxit) break;
+    // restart from the true residual
+    cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, st);
+    double zero = 0.0;
+    cudaMemcpyAsync(s + 6, &zero, 8, cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    conv = false;
   }
   if (P.mean_fix) {
     k_dot_part<<<nblk, PL_NTHR, 0, st>>>(P.rhs, aux.ones, n, part);
@@ -500,7 +518,7 @@ static int run_plain(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaS
     k_sum_final<<<1, PL_NTHR, 0, st>>>(part, nblk, s, 1);
     k_add_const<<<g, 256, 0, st>>>(P.x, s, 0, 1, n);
   }
-  // true residual
+  // true residual of the returned x
   if (int rc = apply_op(P.x, r)) return rc;
   k_sub_from<<<g, 256, 0, st>>>(r, P.rhs, n);
   dot(r, r, 2);
@@ -665,7 +683,7 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
         sub.push_back(hp[i]);
         back.push_back(int(i));
       }
-    if (int rc = run_persistent(sub, dprobs, dmap, dbars, st, LLONG_MAX)) return rc;
+    if (int rc = run_persistent(sub, dprobs, dmap, dbars, st, LLONG_MAX, 0.0)) return rc;
     for (size_t k = 0; k < sub.size(); ++k) hp[back[k]] = sub[k];
   }
   std::vector<SolveState> hs(sps.size());

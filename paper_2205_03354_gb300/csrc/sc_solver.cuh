@@ -49,11 +49,13 @@ struct SolveProb {
   int H_in, H_64;            // planes per apply tile (inner, FP64 tile shapes)
   int ntiles_in, ntiles_64;  // tile counts
   int nchunks;               // vector-phase chunks
+  int chunk;                 // elements per chunk: CG_STEP * 2^k, fixed by the problem size
   int nslot;                 // partial slots per reduction value
   int cta0, ncta;            // CTA group
   double a, b;               // operator a I + b B
   int mixed, mean_fix;
   int vec_in, vec_64;        // 16-byte tile loads legal (alignment checked on host)
+  int vec_v;                 // 16-byte vector-phase loads legal (aligned vectors, npts % 4 == 0)
   double rtol, delta;
   long long maxit;
   const double *w64;         // dense weight box of B (FP64)
@@ -67,7 +69,8 @@ struct SolveProb {
 };
 
 constexpr int CG_NTHR = 128;
-constexpr int CG_CHUNK = CG_NTHR * 32;  // elements per vector-phase chunk
+constexpr int CG_STEP = CG_NTHR * 4;      // elements per vector-phase step (4 per thread)
+constexpr int CG_CHUNK = CG_STEP * 8;     // largest chunk used for sizing scratch (see P.chunk)
 constexpr long long SPIN_LIMIT = 1LL << 24;  // ~1-2 s with the back-off below
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
@@ -90,12 +93,31 @@ struct GroupCtx {
 };
 
 __device__ __forceinline__ double fixed_sum(const double *a, int n, double *red) {
+  // thread t adds slots t, t + 128, ... in order; 8 loads in flight
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += CG_NTHR) s += __ldcg(a + i);
+  int i = threadIdx.x;
+  for (; i + 7 * CG_NTHR < n; i += 8 * CG_NTHR) {
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldcg(a + i + k * CG_NTHR);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (; i < n; i += CG_NTHR) s += __ldcg(a + i);
   return block_sum<CG_NTHR>(s, red);
 }
 
-__device__ bool group_reduce(GroupCtx &G, int nval, int nused, double *out) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// With deadline != 0 the reducing CTA also reads the global timer and
+// publishes out[3] = 1.0 when it is past the deadline, so that every CTA of
+// the group takes the same stop decision.
+__device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *out,
+                             unsigned long long deadline = 0ull) {
   const SolveProb &P = *G.P;
   __shared__ double s_out[4];
   __syncthreads();
@@ -106,6 +128,7 @@ __device__ bool group_reduce(GroupCtx &G, int nval, int nused, double *out) {
       double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
       if (threadIdx.x == 0) s_out[k] = v;
     }
+    if (deadline && threadIdx.x == 0) s_out[3] = global_ns() >= deadline ? 1.0 : 0.0;
     __syncthreads();
   } else {
     G.target += P.ncta;
@@ -122,6 +145,7 @@ __device__ bool group_reduce(GroupCtx &G, int nval, int nused, double *out) {
         double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
         if (threadIdx.x == 0) P.scal[k] = v;
       }
+      if (deadline && threadIdx.x == 0) P.scal[3] = global_ns() >= deadline ? 1.0 : 0.0;
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
@@ -148,10 +172,12 @@ __device__ bool group_reduce(GroupCtx &G, int nval, int nused, double *out) {
     if (threadIdx.x == 0 && ok) {
       __threadfence();
       for (int k = 0; k < nval; ++k) s_out[k] = __ldcg(P.scal + k);
+      if (deadline) s_out[3] = __ldcg(P.scal + 3);
     }
     __syncthreads();
   }
   for (int k = 0; k < nval; ++k) out[k] = s_out[k];
+  if (deadline) out[3] = s_out[3];
   __syncthreads();
   return ok;
 }
@@ -273,7 +299,8 @@ __device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, d
   }
 }
 
-// Vector phases over fixed chunks.  kind:
+// Vector phases over fixed chunks of P.chunk elements (chunk c is always
+// handled by group rank c % ncta, in a fixed element order).  KIND:
 //  0: init     rh = TI(r), p = rh, d = 0 (mixed); partials rh.rh, rhs.rhs, sum(rhs)
 //  1: update   d += alpha p, rh -= alpha q; partial rh.rh
 //  2: direction p = rh + beta p
@@ -281,61 +308,160 @@ __device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, d
 //  4: to-inner rh = TI(r); partial rh.rh
 //  5: sum(x)   partial
 //  6: shift    x += c
-template <typename TI>
-__device__ void phase_vec(const SolveProb &P, int rank, int kind, double s1, double *red) {
+// Each thread moves 4 consecutive elements per step (16-byte loads for FP32,
+// two for FP64) and keeps up to 4 steps in flight; all loads go through L2.
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
+  if (sizeof(T) == 4) {
+    const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+    v[0] = T(t.x); v[1] = T(t.y); v[2] = T(t.z); v[3] = T(t.w);
+  } else {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = T(a.x); v[1] = T(a.y); v[2] = T(b.x); v[3] = T(b.y);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4]) {
+  if (sizeof(T) == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(float(v[0]), float(v[1]), float(v[2]), float(v[3]));
+  } else {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(double(v[0]), double(v[1]));
+    reinterpret_cast<double2 *>(p)[1] = make_double2(double(v[2]), double(v[3]));
+  }
+}
+
+template <typename TI, int KIND>
+__device__ __forceinline__ void vec_elems(const SolveProb &P, long long i, int n, double s1, double &a0,
+                                          double &a1, double &a2) {
+  // scalar fallback for ragged or unaligned data, n <= 4 elements from i
+  TI *rh = static_cast<TI *>(P.rh), *p = static_cast<TI *>(P.p), *q = static_cast<TI *>(P.q),
+     *d = static_cast<TI *>(P.d);
+  for (int k = 0; k < n; ++k, ++i) {
+    if (KIND == 0) {
+      const TI v = TI(__ldcg(P.r + i));
+      rh[i] = v;
+      p[i] = v;
+      if (P.mixed) d[i] = TI(0);
+      const double bv = __ldcg(P.rhs + i);
+      a0 += double(v) * double(v);
+      a1 += bv * bv;
+      a2 += bv;
+    } else if (KIND == 1) {
+      const TI al = TI(s1);
+      const TI pv = __ldcg(p + i);
+      d[i] = __ldcg(d + i) + al * pv;
+      const TI v = __ldcg(rh + i) - al * __ldcg(q + i);
+      rh[i] = v;
+      a0 += double(v) * double(v);
+    } else if (KIND == 2) {
+      p[i] = __ldcg(rh + i) + TI(s1) * __ldcg(p + i);
+    } else if (KIND == 3) {
+      P.x[i] = __ldcg(P.x + i) + double(__ldcg(d + i));
+      d[i] = TI(0);
+    } else if (KIND == 4) {
+      const TI v = TI(__ldcg(P.r + i));
+      rh[i] = v;
+      a0 += double(v) * double(v);
+    } else if (KIND == 5) {
+      a0 += __ldcg(P.x + i);
+    } else {
+      P.x[i] = __ldcg(P.x + i) + s1;
+    }
+  }
+}
+
+template <typename TI, int KIND>
+__device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) {
   TI *rh = static_cast<TI *>(P.rh), *p = static_cast<TI *>(P.p), *q = static_cast<TI *>(P.q),
      *d = static_cast<TI *>(P.d);
   for (int c = rank; c < P.nchunks; c += P.ncta) {
-    const long long e0 = (long long)c * CG_CHUNK;
-    const long long e1 = min(e0 + CG_CHUNK, P.npts);
+    const long long e0 = (long long)c * P.chunk;
+    const long long e1 = min(e0 + P.chunk, P.npts);
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (long long i = e0 + threadIdx.x; i < e1; i += CG_NTHR) {
-      switch (kind) {
-        case 0: {
-          const TI v = TI(__ldcg(P.r + i));
-          rh[i] = v;
-          p[i] = v;
-          if (P.mixed) d[i] = TI(0);
-          a0 += double(v) * double(v);
-          const double bv = __ldcg(P.rhs + i);
-          a1 += bv * bv;
-          a2 += bv;
-          break;
-        }
-        case 1: {
+    if (P.vec_v && e1 - e0 == P.chunk) {
+      const int nsteps = P.chunk / CG_STEP;
+#pragma unroll 4
+      for (int k = 0; k < nsteps; ++k) {
+        const long long i = e0 + 4LL * (k * CG_NTHR + threadIdx.x);
+        if (KIND == 0) {
+          double r[4], b[4];
+          ld4(P.r + i, r);
+          ld4(P.rhs + i, b);
+          TI v[4], z[4] = {TI(0), TI(0), TI(0), TI(0)};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            v[j] = TI(r[j]);
+            a0 += double(v[j]) * double(v[j]);
+            a1 += b[j] * b[j];
+            a2 += b[j];
+          }
+          st4(rh + i, v);
+          st4(p + i, v);
+          if (P.mixed) st4(d + i, z);
+        } else if (KIND == 1) {
+          TI pv[4], dv[4], rv[4], qv[4];
+          ld4(p + i, pv);
+          ld4(d + i, dv);
+          ld4(rh + i, rv);
+          ld4(q + i, qv);
           const TI al = TI(s1);
-          const TI pv = __ldcg(p + i);
-          d[i] = __ldcg(d + i) + al * pv;
-          const TI v = __ldcg(rh + i) - al * __ldcg(q + i);
-          rh[i] = v;
-          a0 += double(v) * double(v);
-          break;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            dv[j] = dv[j] + al * pv[j];
+            rv[j] = rv[j] - al * qv[j];
+            a0 += double(rv[j]) * double(rv[j]);
+          }
+          st4(d + i, dv);
+          st4(rh + i, rv);
+        } else if (KIND == 2) {
+          TI pv[4], rv[4];
+          ld4(p + i, pv);
+          ld4(rh + i, rv);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) pv[j] = rv[j] + TI(s1) * pv[j];
+          st4(p + i, pv);
+        } else if (KIND == 3) {
+          double xv[4];
+          TI dv[4], z[4] = {TI(0), TI(0), TI(0), TI(0)};
+          ld4(P.x + i, xv);
+          ld4(d + i, dv);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[j] += double(dv[j]);
+          st4(P.x + i, xv);
+          st4(d + i, z);
+        } else if (KIND == 4) {
+          double r[4];
+          ld4(P.r + i, r);
+          TI v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            v[j] = TI(r[j]);
+            a0 += double(v[j]) * double(v[j]);
+          }
+          st4(rh + i, v);
+        } else if (KIND == 5) {
+          double xv[4];
+          ld4(P.x + i, xv);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) a0 += xv[j];
+        } else {
+          double xv[4];
+          ld4(P.x + i, xv);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[j] += s1;
+          st4(P.x + i, xv);
         }
-        case 2:
-          p[i] = __ldcg(rh + i) + TI(s1) * __ldcg(p + i);
-          break;
-        case 3:
-          P.x[i] = __ldcg(P.x + i) + double(__ldcg(d + i));
-          d[i] = TI(0);
-          break;
-        case 4: {
-          const TI v = TI(__ldcg(P.r + i));
-          rh[i] = v;
-          a0 += double(v) * double(v);
-          break;
-        }
-        case 5:
-          a0 += __ldcg(P.x + i);
-          break;
-        case 6:
-          P.x[i] = __ldcg(P.x + i) + s1;
-          break;
       }
+    } else {
+      for (long long i = e0 + 4LL * threadIdx.x; i < e1; i += 4LL * CG_NTHR)
+        vec_elems<TI, KIND>(P, i, int(min(4LL, e1 - i)), s1, a0, a1, a2);
     }
-    if (kind == 0 || kind == 1 || kind == 4 || kind == 5) {
+    if (KIND == 0 || KIND == 1 || KIND == 4 || KIND == 5) {
       const double t0 = block_sum<CG_NTHR>(a0, red);
       if (threadIdx.x == 0) P.part[c] = t0;
-      if (kind == 0) {
+      if (KIND == 0) {
         const double t1 = block_sum<CG_NTHR>(a1, red);
         if (threadIdx.x == 0) P.part[P.nslot + c] = t1;
         const double t2 = block_sum<CG_NTHR>(a2, red);
@@ -348,9 +474,15 @@ __device__ void phase_vec(const SolveProb &P, int rank, int kind, double s1, dou
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
 
 // Runs one problem for at most `budget` inner iterations.
+// Runs one problem for at most `budget` inner iterations and, when slice_ns
+// is nonzero, for about that long (the global timer is compared once per
+// iteration by the reducing CTA, so the whole group stops together); the
+// state is saved for the next launch.
 template <typename TI, int NDIM, int R>
-__device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget) {
+__device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
+                       unsigned long long slice_ns) {
   const SolveProb &P = *G.P;
+  const unsigned long long deadline = slice_ns ? global_ns() + slice_ns : 0ull;
   SolveState &S = *P.st;
   double red_out[4];
   double *red = G.red;
@@ -365,7 +497,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget) {
     // r = rhs - A x0 (FP64); rh = r; p = rh
     phase_resid<NDIM, R>(P, G.rank, smem, red);
     if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
-    phase_vec<TI>(P, G.rank, 0, 0.0, red);
+    phase_vec<TI, 0>(P, G.rank, 0.0, red);
     if (!group_reduce(G, 3, P.nchunks, red_out)) return;
     rr = red_out[0];
     bnorm = sqrt(red_out[1]);
@@ -395,7 +527,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget) {
     }
     const double alpha = rr / pq;
     // B: d += alpha p, rh -= alpha q, rh.rh
-    phase_vec<TI>(P, G.rank, 1, alpha, red);
+    phase_vec<TI, 1>(P, G.rank, alpha, red);
     if (!group_reduce(G, 1, P.nchunks, red_out)) return;
     double rr_new = red_out[0];
     ++iters;
@@ -406,46 +538,51 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget) {
       phase = 3;
       break;
     }
-    if (P.mixed) {
-      if (rn <= P.delta * rmax || rn <= tol * bnorm) {
-        // reliable update: x += d in FP64, true residual, new rh
-        phase_vec<TI>(P, G.rank, 3, 0.0, red);
+    // refresh: mixed -- every `delta` decrease or at the tolerance; FP64 --
+    // at the tolerance.  The FP64 true residual replaces the recurrence one;
+    // convergence is only declared on it.
+    const bool refresh = P.mixed ? (rn <= P.delta * rmax || rn <= tol * bnorm) : (rn <= tol * bnorm);
+    if (refresh) {
+      if (P.mixed) {  // x += d in FP64
+        phase_vec<TI, 3>(P, G.rank, 0.0, red);
         if (!group_reduce(G, 0, 0, red_out)) return;
-        phase_resid<NDIM, R>(P, G.rank, smem, red);
-        if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
-        ++outer;
-        rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
-        if (rel <= tol) {
-          phase = 3;
-          break;
-        }
-        phase_vec<TI>(P, G.rank, 4, 0.0, red);
+      }
+      phase_resid<NDIM, R>(P, G.rank, smem, red);
+      if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
+      ++outer;
+      rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
+      if (rel <= tol) {
+        phase = 3;
+        break;
+      }
+      if (P.mixed) {
+        phase_vec<TI, 4>(P, G.rank, 0.0, red);
         if (!group_reduce(G, 1, P.nchunks, red_out)) return;
         rr_new = red_out[0];
-        rmax = sqrt(rr_new);
+      } else {
+        rr_new = red_out[0];  // r (== rh) now holds the true residual
       }
-    } else if (rn <= tol * bnorm) {
-      phase = 3;  // FP64 recurrence residual met the tolerance
-      break;
+      rmax = sqrt(rr_new);
     }
     beta = rr_new / rr;
     rr = rr_new;
     // C: p = rh + beta p
-    phase_vec<TI>(P, G.rank, 2, beta, red);
-    if (!group_reduce(G, 0, 0, red_out)) return;
+    phase_vec<TI, 2>(P, G.rank, beta, red);
+    if (!group_reduce(G, 0, 0, red_out, deadline)) return;
+    if (deadline && red_out[3] != 0.0) break;
   }
 
   if (phase == 3) {
     // finish: FP64 x (mixed: fold d), optional mean fix, true residual
     if (P.mixed) {
-      phase_vec<TI>(P, G.rank, 3, 0.0, red);
+      phase_vec<TI, 3>(P, G.rank, 0.0, red);
       if (!group_reduce(G, 0, 0, red_out)) return;
     }
     if (P.mean_fix) {
-      phase_vec<TI>(P, G.rank, 5, 0.0, red);
+      phase_vec<TI, 5>(P, G.rank, 0.0, red);
       if (!group_reduce(G, 1, P.nchunks, red_out)) return;
       const double c = (sumb - red_out[0]) / double(P.npts);
-      phase_vec<TI>(P, G.rank, 6, c, red);
+      phase_vec<TI, 6>(P, G.rank, c, red);
       if (!group_reduce(G, 0, 0, red_out)) return;
     }
     phase_resid<NDIM, R>(P, G.rank, smem, red);

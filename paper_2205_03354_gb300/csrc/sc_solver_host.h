@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include "../../include/stencilcomp.h"
+
 namespace sc {
 
 struct SolveProb;  // sc_solver.cuh
@@ -28,7 +30,33 @@ struct ProbAux {
   double *ones;     // vector of ones (plain mean fix)
 };
 
+// Sub-allocates 256-byte aligned pieces of a caller buffer (base == nullptr:
+// sizing only).
+struct Carver {
+  char *base;
+  size_t off = 0, cap;
+  Carver(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+  void *take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void *p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
 double kappa_estimate(const ProbSpec &sp, double h);
 int max_group_ctas(bool mixed);
+int bvp_spec(const sc_bvp *b, ProbSpec &sp);
+// Work-space layout of one problem (sizes only when cv.base == nullptr).
+void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux);
+// Weights, initial state and alignment flags of one problem (synchronous).
+int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
+// Right-hand side b = g - A(ring) and x = 0 of a plate problem (enqueued).
+int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
+// Runs the persistent engine over `hp` (both precision classes) for at most
+// `budget` iterations or `slice_ms` milliseconds per launch (0: no limit);
+// synchronous.  dprobs/dmap/dbars: device descriptor space.
+int run_persistent(std::vector<SolveProb> &hp, SolveProb *dprobs, int *dmap, unsigned *dbars,
+                   cudaStream_t st, long long budget, double slice_ms);
 
 }  // namespace sc

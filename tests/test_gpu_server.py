@@ -1,0 +1,96 @@
+"""The serving loop: continuous batching of plate-problem solves.
+
+Each result obtained through the server, while other requests of other sizes
+and dimensions are in flight, must be the same as the result of solving that
+request alone (same precision): bit for bit, since the engine's reductions
+do not depend on the batch.  A small arena forces queueing and admission as
+memory frees up.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.libutil import ensure_built  # noqa: E402
+
+ensure_built()
+import paper_2205_03354_gb300 as sc  # noqa: E402
+from synth_inputs import manufactured  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _case(n, ndim, ks):
+    m = manufactured.bvp_case(n, ndim, 2, ks)
+    return np.ascontiguousarray(m["g"]), np.ascontiguousarray(m["u_padded"])
+
+
+def _solo(f, g, prec):
+    ft, gt = torch.from_numpy(f).to(DEV), torch.from_numpy(g).to(DEV)
+    x = torch.empty(f.shape, dtype=torch.float64, device=DEV)
+    info = sc.solve_biharmonic(ft, gt, x, prec=prec, rtol=1e-10)
+    return x.cpu().numpy(), info
+
+
+SPECS = [(40, 2, (1, 1)), (24, 2, (3, 2)), (12, 3, (1, 2, 1)), (64, 2, (2, 5)), (17, 2, (1, 1)),
+         (10, 3, (2, 1, 3)), (33, 2, (4, 4)), (20, 3, (1, 1, 1))]
+
+
+def test_results_same_alone_and_in_the_mix():
+    arena = torch.empty(512 << 20, dtype=torch.uint8, device=DEV)
+    srv = sc.Server(arena, max_active=64, slice_ms=1.0)
+    try:
+        tickets, bufs = [], []
+        for n, nd, ks in SPECS:
+            f, g = _case(n, nd, ks)
+            x = np.full(f.shape, np.nan)
+            tickets.append(srv.submit(f, g, x, prec="auto"))
+            bufs.append((f, g, x))
+        srv.drain(300.0)
+        for t, (f, g, x) in zip(tickets, bufs):
+            res = srv.poll(t)
+            assert res is not None and res["status"] == 0 and res["rel_res"] <= 1e-10, res
+            assert res["latency_s"] >= res["queue_s"] >= 0.0
+            solo, info = _solo(f, g, res["prec"])
+            assert info["iters"] == res["iters"]
+            assert np.array_equal(solo, x)
+    finally:
+        srv.close()
+
+
+def test_small_arena_queues_and_admits_as_memory_frees():
+    f0, g0 = _case(64, 2, (1, 1))
+    need = sc.request_bytes(sc.make_request(f0, g0, np.empty_like(f0)))
+    arena = torch.empty(2 * need + (4 << 20), dtype=torch.uint8, device=DEV)  # about two at a time
+    srv = sc.Server(arena, max_active=8, slice_ms=0.5)
+    try:
+        tickets, bufs = [], []
+        for k in range(6):
+            f, g = _case(64, 2, (1 + k % 3, 1))
+            x = np.full(f.shape, np.nan)
+            tickets.append(srv.submit(f, g, x, prec="f64"))
+            bufs.append(x)
+        done = {}
+        import time
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 300:
+            for t in tickets:
+                if t not in done:
+                    r = srv.poll(t)
+                    if r is not None:
+                        done[t] = r
+            time.sleep(0.002)
+        assert len(done) == 6
+        assert all(r["status"] == 0 and r["rel_res"] <= 1e-10 for r in done.values())
+        assert max(r["queue_s"] for r in done.values()) > 0.0  # some had to wait for memory
+        assert all(np.isfinite(x).all() for x in bufs)
+        # unknown ticket and oversized request
+        with pytest.raises(sc.ScError):
+            srv.poll(10 ** 9)
+        fb, gb = _case(400, 2, (1, 1))
+        with pytest.raises(sc.ScError) as e:
+            srv.submit(fb, gb, np.empty_like(fb))
+        assert e.value.status == 2  # SC_ENOMEM
+    finally:
+        srv.close()
