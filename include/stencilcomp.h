@@ -142,6 +142,35 @@ int sc_apply_composed(const sc_stencil *s, int32_t dtype, int32_t bc, const int6
                       int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
                       sc_stream_t stream);
 
+/* The composed operator C = B(A) evaluated in nested form, y = B(A x) (the
+ * double sum of Eq. C=B(A)), from the two factors outer = B and inner = A
+ * instead of the composed weights: A is applied on the grid extended by
+ * B's radius into a temporary in work_dev, then B.  Same operator and
+ * boundary semantics as sc_apply_composed(compose(B, A)) up to rounding
+ * (the two factors' weights are rounded separately); fewer arithmetic
+ * operations when both factors are sparse (2 x 13 instead of 73 FMAs per
+ * point for the 3D fourth-order Lap o Lap), at the price of the temporary's
+ * traffic.  For SC_BC_GHOSTED, x carries a ring of width
+ * outer->radius + inner->radius.  work_bytes >=
+ * sc_apply_composition_work_bytes(...).
+ *
+ * arith = SC_ARITH_NATIVE evaluates in dtype.  arith = SC_ARITH_PAIR (dtype
+ * SC_F64 only) evaluates Laplacian factors -- symmetric star stencils with
+ * one integer numerator per distance, radius 1 or 2 -- in pairs of FP32
+ * numbers with error-free transformations (GB300 has 64x more FP32 than
+ * FP64 FMA throughput): the doubles are split exactly with integer bit
+ * operations and the result is rebuilt exactly; the error is a few units of
+ * 2^-48 of sum |w x|, inside the FP64 apply tolerance.  Nonzero inputs with
+ * magnitude outside [2^-74, 2^100] set a device flag and the native FP64
+ * passes recompute the result (they are always enqueued and return at once
+ * when the flag is clear).  Other factor shapes fall back to SC_ARITH_NATIVE. */
+typedef enum { SC_ARITH_NATIVE = 0, SC_ARITH_PAIR = 1 } sc_arith;
+size_t sc_apply_composition_work_bytes(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype,
+                                        int32_t bc, const int64_t *dims);
+int sc_apply_composition(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                         const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                         void *work_dev, size_t work_bytes, int32_t arith, sc_stream_t stream);
+
 /* Same as sc_apply_composed, with x and y in HOST memory: copies x to the
  * device work space, applies, copies y back and waits for the stream.
  * work_bytes >= sc_apply_host_work_bytes(...). */

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "sc_apply.cuh"
+#include "sc_apply_df.h"
 #include "sc_apply_host.h"
 #include "sc_internal.h"
 
@@ -15,8 +16,9 @@ namespace sc {
 template <typename T, int NDIM, int R, int CLS>
 __global__ void __launch_bounds__(FlatApply<T, NDIM, R, CLS>::NTHR)
     flat_apply_kernel(const T *__restrict__ x, T *__restrict__ y, ApplyGeom g,
-                      const __grid_constant__ BoxWeights<T, NDIM, R> W) {
+                      const __grid_constant__ BoxWeights<T, NDIM, R> W, const int *__restrict__ guard) {
   using K = FlatApply<T, NDIM, R, CLS>;
+  if (guard && __ldcg(guard) == 0) return;  // conditional fallback pass: nothing to redo
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *smem = reinterpret_cast<T *>(smem_raw);
   const int x0 = blockIdx.x * K::BX;
@@ -37,16 +39,41 @@ int num_sms() {
   return g_num_sms;
 }
 
-// Output planes per CTA: enough CTAs for several waves of resident blocks,
-// long enough runs to amortise the 2R halo planes.
-static int choose_h(long long tiles_per_plane, int nplanes, int R, int override_h) {
+int wave_planes(long long tiles_xy, int nplanes, int R, long long slots, int hmin) {
+  // The kernels are throughput-bound per SM: the run time follows the
+  // busiest SM's work, ceil(CTAs / SMs) * (H + 2R).  Candidates must fill
+  // every resident slot at least once (else SMs idle); small grids that
+  // cannot take the smallest H.
+  if (nplanes <= 1) return 1;
+  const long long sms = num_sms();
+  long long best_h = -1, small_h = nplanes;
+  double best = 1e300;
+  for (long long zb = 1; zb <= nplanes; ++zb) {
+    const long long h = (nplanes + zb - 1) / zb;
+    if (h < hmin && zb > 1) break;
+    small_h = h;
+    const long long ctas = tiles_xy * ((nplanes + h - 1) / h);
+    if (ctas >= slots) {
+      const double cost = double((ctas + sms - 1) / sms) * double(h + 2 * R);
+      if (cost < best * 0.999) {
+        best = cost;
+        best_h = h;
+      }
+    }
+    if (h == hmin) break;
+  }
+  return int(best_h > 0 ? best_h : small_h);
+}
+
+// Output planes per CTA (see wave_planes).
+template <typename KERN>
+static int choose_h(KERN kern, int nthr, size_t smem, long long tiles_per_plane, int nplanes, int R,
+                    int override_h) {
   if (override_h > 0) return std::min(override_h, nplanes);
-  const long long target = 8LL * num_sms();
-  long long h = (tiles_per_plane * nplanes + target - 1) / target;
-  h = std::max<long long>(h, 4 * R);
-  h = std::min<long long>(h, 256);
-  h = std::min<long long>(h, nplanes);
-  return int(std::max<long long>(h, 1));
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nthr, smem);
+  const long long slots = (long long)std::max(occ, 1) * num_sms();
+  return wave_planes(tiles_per_plane, nplanes, R, slots, std::max(4 * R, 8));
 }
 
 static int g_h_override = 0;
@@ -81,7 +108,13 @@ static int launch_flat(const ApplyReq &q, const T *wts_sparse, cudaStream_t st) 
   const int ns = NDIM == 3 ? g.nz : g.ny;
   const long long tiles = (long long)((g.nx + K::BX - 1) / K::BX) *
                           (NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : 1);
-  g.H = choose_h(tiles, ns, R, g_h_override);
+  auto kern = flat_apply_kernel<T, NDIM, R, CLS>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
+    attr_set = true;
+  }
+  g.H = choose_h(kern, K::NTHR, K::SMEM, tiles, ns, R, g_h_override);
   const uintptr_t xa = reinterpret_cast<uintptr_t>(q.x), ya = reinterpret_cast<uintptr_t>(q.y);
   bool vec = (xa % 16 == 0) && (ya % 16 == 0) && (g.nx % K::CH == 0);
   if (q.bc == SC_BC_GHOSTED) vec = vec && (q.s->radius == R) && ((R - K::HX) % K::CH == 0) &&
@@ -92,13 +125,7 @@ static int launch_flat(const ApplyReq &q, const T *wts_sparse, cudaStream_t st) 
     return fail(SC_EINVAL, "ghosted apply needs the class radius to equal the stencil radius");
   dim3 grid((g.nx + K::BX - 1) / K::BX, NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : (ns + g.H - 1) / g.H,
             NDIM == 3 ? (ns + g.H - 1) / g.H : 1);
-  auto kern = flat_apply_kernel<T, NDIM, R, CLS>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
-    attr_set = true;
-  }
-  kern<<<grid, K::NTHR, K::SMEM, st>>>(static_cast<const T *>(q.x), static_cast<T *>(q.y), g, W);
+  kern<<<grid, K::NTHR, K::SMEM, st>>>(static_cast<const T *>(q.x), static_cast<T *>(q.y), g, W, q.guard);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SC_ECUDA, "apply launch: %s", cudaGetErrorString(e));
   return SC_OK;
@@ -112,9 +139,10 @@ static int dispatch(const ApplyReq &q, cudaStream_t st) {
                             : weights_f32(q.s, q.h_num, q.h_den, reinterpret_cast<float *>(w.data()));
   if (rc) return rc;
   const int nd = q.s->ndim;
-  bool c2 = true, c4 = true;
+  bool c2 = true, c4 = true, star = true;
   for (int k = 0; k < q.s->npts; ++k) {
     const int dx = q.s->off[k][0], dy = q.s->off[k][1], dz = q.s->off[k][2];
+    star = star && in_support<CLS_STAR, 4>(dx, dy, dz);
     c2 = c2 && std::max({std::abs(dx), std::abs(dy), std::abs(dz)}) <= 2 &&
          in_support<CLS_CROSS2, 2>(dx, dy, dz);
     c4 = c4 && std::max({std::abs(dx), std::abs(dy), std::abs(dz)}) <= 4 &&
@@ -124,12 +152,16 @@ static int dispatch(const ApplyReq &q, cudaStream_t st) {
   // the ghosted layout has a ring of the stencil's radius; the class radius
   // must equal it for the strides to match
   if (nd == 2) {
+    if (star && r == 1) return launch_flat<T, 2, 1, CLS_STAR>(q, w.data(), st);
+    if (star && r == 2) return launch_flat<T, 2, 2, CLS_STAR>(q, w.data(), st);
     if (c2 && (q.bc != SC_BC_GHOSTED || r == 2)) return launch_flat<T, 2, 2, CLS_CROSS2>(q, w.data(), st);
     if (c4 && (q.bc != SC_BC_GHOSTED || r == 4)) return launch_flat<T, 2, 4, CLS_CROSS2>(q, w.data(), st);
     if (r <= 1 && (q.bc != SC_BC_GHOSTED || r == 1)) return launch_flat<T, 2, 1, CLS_BOX>(q, w.data(), st);
     if (r <= 2 && (q.bc != SC_BC_GHOSTED || r == 2)) return launch_flat<T, 2, 2, CLS_BOX>(q, w.data(), st);
     if (r <= 4 && (q.bc != SC_BC_GHOSTED || r == 4)) return launch_flat<T, 2, 4, CLS_BOX>(q, w.data(), st);
   } else {
+    if (star && r == 1) return launch_flat<T, 3, 1, CLS_STAR>(q, w.data(), st);
+    if (star && r == 2) return launch_flat<T, 3, 2, CLS_STAR>(q, w.data(), st);
     if (c2 && (q.bc != SC_BC_GHOSTED || r == 2)) return launch_flat<T, 3, 2, CLS_CROSS2>(q, w.data(), st);
     if (c4 && (q.bc != SC_BC_GHOSTED || r == 4)) return launch_flat<T, 3, 4, CLS_CROSS2>(q, w.data(), st);
     if (r <= 1 && (q.bc != SC_BC_GHOSTED || r == 1)) return launch_flat<T, 3, 1, CLS_BOX>(q, w.data(), st);
@@ -171,6 +203,104 @@ size_t grid_elems(const sc_stencil *s, int bc, const int64_t *dims, bool input) 
 
 void set_apply_planes_override(int h) { g_h_override = h; }
 
+// xp = x surrounded by a zero ring of width R (all dims).
+template <typename T>
+__global__ void k_pad_zero(const T *__restrict__ x, T *__restrict__ xp, int ndim, long long nx, long long ny,
+                           long long nz, int R) {
+  const long long px = nx + 2 * R, py = ny + 2 * R, pz = ndim == 3 ? nz + 2 * R : 1;
+  const long long n = px * py * pz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long ix = i % px - R, iy = (i / px) % py - R, iz = ndim == 3 ? i / (px * py) - R : 0;
+    const bool in = ix >= 0 && ix < nx && iy >= 0 && iy < ny && iz >= 0 && iz < (ndim == 3 ? nz : 1);
+    xp[i] = in ? x[(iz * ny + iy) * nx + ix] : T(0);
+  }
+}
+
+static size_t elems_ext(int ndim, const int64_t *dims, int ext) {
+  size_t n = 1;
+  for (int a = 0; a < ndim; ++a) n *= size_t(dims[a] + 2 * ext);
+  return n;
+}
+
+size_t composition_work_bytes(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims) {
+  const size_t es = dtype == SC_F64 ? 8 : 4;
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  size_t b = up(elems_ext(A->ndim, dims, B->radius) * es);
+  if (bc == SC_BC_ZERO) b += up(elems_ext(A->ndim, dims, A->radius + B->radius) * es);
+  return b + 256;  // + the out-of-range flag of the pair-arithmetic path
+}
+
+// y = B(A x): the inner stencil on the grid extended by B's radius into a
+// temporary, then the outer stencil (Eq. C=B(A), nested form).
+int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims,
+                        int64_t h_num, int64_t h_den, const void *x, void *y, void *work, cudaStream_t st,
+                        int arith) {
+  const int nd = A->ndim, rA = A->radius, rB = B->radius;
+  const size_t es = dtype == SC_F64 ? 8 : 4;
+  char *w = static_cast<char *>(work);
+  void *t = w;
+  const size_t tb = (elems_ext(nd, dims, rB) * es + 255) & ~size_t(255);
+  int64_t dext[3] = {1, 1, 1};
+  for (int a = 0; a < nd; ++a) dext[a] = dims[a] + 2 * rB;
+  const size_t xpb = bc == SC_BC_ZERO ? (elems_ext(nd, dims, rA + rB) * es + 255) & ~size_t(255) : 0;
+  int *flag = reinterpret_cast<int *>(w + tb + xpb);
+  // pair arithmetic for FP64 Laplacian compositions (see sc_apply_df.cu)
+  float ca[3], cb[3];
+  const bool pair = arith == SC_ARITH_PAIR && dtype == SC_F64 && rA == rB && star_int_form(A, ca, ca + 1, ca + 2) &&
+                    star_int_form(B, cb, cb + 1, cb + 2) && A->hpow == B->hpow && dims[0] % 2 == 0 &&
+                    (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
+                    (bc == SC_BC_PERIODIC || rA == 2);
+  double scale = 1.0;
+  if (pair) {
+    // exact rational 1 / (den_A den_B h^(pA + pB)), rounded once
+    sc_stencil one;
+    std::memset(&one, 0, sizeof(one));
+    one.ndim = nd;
+    one.npts = 1;
+    one.hpow = A->hpow + B->hpow;
+    one.den = 1;
+    one.num[0] = 1;
+    double unit = 0.0;
+    if (int rc = weights_f64(&one, h_num, h_den, &unit)) return rc;
+    scale = unit / (double(A->den) * double(B->den));  // den products are small integers: exact
+    if (!(double(A->den) * double(B->den) < 9007199254740992.0)) return fail(SC_EOVERFLOW, "denominator");
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+  }
+  if (bc == SC_BC_PERIODIC) {
+    if (pair) {
+      if (int rc = df_composition_enqueue(nd, rA, x, t, y, dims, dims, SC_BC_PERIODIC, ca, cb, scale, flag, st))
+        return rc;
+    }
+    ApplyReq qa{A, dtype, SC_BC_PERIODIC, dims, h_num, h_den, x, t, pair ? flag : nullptr};
+    if (int rc = apply_enqueue(qa, st)) return rc;
+    ApplyReq qb{B, dtype, SC_BC_PERIODIC, dims, h_num, h_den, t, y, pair ? flag : nullptr};
+    return apply_enqueue(qb, st);
+  }
+  const void *xin = x;
+  if (bc == SC_BC_ZERO) {
+    void *xp = w + tb;
+    const size_t n = elems_ext(nd, dims, rA + rB);
+    const int g = int(std::min<size_t>((n + 255) / 256, 8 * size_t(num_sms())));
+    if (dtype == SC_F64)
+      k_pad_zero<double><<<g, 256, 0, st>>>(static_cast<const double *>(x), static_cast<double *>(xp), nd,
+                                             dims[0], dims[1], nd == 3 ? dims[2] : 1, rA + rB);
+    else
+      k_pad_zero<float><<<g, 256, 0, st>>>(static_cast<const float *>(x), static_cast<float *>(xp), nd,
+                                            dims[0], dims[1], nd == 3 ? dims[2] : 1, rA + rB);
+    xin = xp;
+  }
+  // x (n + 2(rA + rB)) -> t (n + 2 rB) -> y (n)
+  if (pair) {
+    if (int rc = df_composition_enqueue(nd, rA, xin, t, y, dext, dims, SC_BC_GHOSTED, ca, cb, scale, flag, st))
+      return rc;
+  }
+  ApplyReq qa{A, dtype, SC_BC_GHOSTED, dext, h_num, h_den, xin, t, pair ? flag : nullptr};
+  if (int rc = apply_enqueue(qa, st)) return rc;
+  ApplyReq qb{B, dtype, SC_BC_GHOSTED, dims, h_num, h_den, t, y, pair ? flag : nullptr};
+  return apply_enqueue(qb, st);
+}
+
 }  // namespace sc
 
 using namespace sc;
@@ -185,6 +315,32 @@ int sc_apply_composed(const sc_stencil *s, int32_t dtype, int32_t bc, const int6
   if (x_dev == y_dev) return fail(SC_EINVAL, "x and y must not overlap");
   ApplyReq q{s, dtype, bc, dims, h_num, h_den, x_dev, y_dev};
   int rc = apply_enqueue(q, (cudaStream_t)stream);
+  if (!rc) clear_error();
+  return rc;
+}
+
+size_t sc_apply_composition_work_bytes(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype,
+                                        int32_t bc, const int64_t *dims) {
+  if (validate_apply(outer, dtype, bc, dims, 1, 1) || validate_apply(inner, dtype, bc, dims, 1, 1)) return 0;
+  if (outer->ndim != inner->ndim) return 0;
+  return composition_work_bytes(outer, inner, dtype, bc, dims);
+}
+
+int sc_apply_composition(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                         const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                         void *work_dev, size_t work_bytes, int32_t arith, sc_stream_t stream) {
+  if (arith != SC_ARITH_NATIVE && arith != SC_ARITH_PAIR) return fail(SC_EINVAL, "unknown arith %d", arith);
+  if (int rc = validate_apply(outer, dtype, bc, dims, h_num, h_den)) return rc;
+  if (int rc = validate_apply(inner, dtype, bc, dims, h_num, h_den)) return rc;
+  if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
+  if (outer->radius + inner->radius > SC_MAX_APPLY_RADIUS)
+    return fail(SC_EINVAL, "composed radius %d > %d", outer->radius + inner->radius, SC_MAX_APPLY_RADIUS);
+  if (!x_dev || !y_dev || !work_dev) return fail(SC_EINVAL, "null device pointer");
+  if (x_dev == y_dev) return fail(SC_EINVAL, "x and y must not overlap");
+  const size_t need = composition_work_bytes(outer, inner, dtype, bc, dims);
+  if (work_bytes < need) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, need);
+  int rc = composition_enqueue(outer, inner, dtype, bc, dims, h_num, h_den, x_dev, y_dev, work_dev,
+                               (cudaStream_t)stream, arith);
   if (!rc) clear_error();
   return rc;
 }

@@ -21,15 +21,19 @@
 
 namespace sc {
 
-enum { CLS_BOX = 0, CLS_CROSS2 = 1 };
+enum { CLS_BOX = 0, CLS_CROSS2 = 1, CLS_STAR = 2 };
 
-// Is (dx, dy, dz) in the support class?  CROSS2(R): at most one nonzero
-// component (|.| <= R), or exactly two with both |.| <= R/2 -- the support
-// of Lap o Lap for a Laplacian whose 1D stencils have radius R/2.
+// Is (dx, dy, dz) in the support class?  STAR(R): at most one nonzero
+// component (a sum of 1D stencils along the axes, e.g. a Laplacian).
+// CROSS2(R): STAR(R) plus the points with exactly two nonzero components
+// both |.| <= R/2 -- the support of Lap o Lap for a Laplacian whose 1D
+// stencils have radius R/2.  BOX(R): everything within radius R.
 template <int CLS, int R>
 __host__ __device__ constexpr bool in_support(int dx, int dy, int dz) {
   return CLS == CLS_BOX
              ? true
+             : CLS == CLS_STAR
+             ? (dx != 0) + (dy != 0) + (dz != 0) <= 1
              : ((dx != 0) + (dy != 0) + (dz != 0) <= 1
                     ? true
                     : ((dx != 0) + (dy != 0) + (dz != 0) == 2 && (dx < 0 ? -dx : dx) <= R / 2 &&

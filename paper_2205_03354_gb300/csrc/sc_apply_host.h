@@ -17,6 +17,7 @@ struct ApplyReq {
   int64_t h_num, h_den;
   const void *x;
   void *y;
+  const int *guard = nullptr;  // if set: the kernel only works when *guard != 0
 };
 
 int validate_apply(const sc_stencil *s, int dtype, int bc, const int64_t *dims, int64_t h_num,
@@ -25,6 +26,11 @@ int validate_apply(const sc_stencil *s, int dtype, int bc, const int64_t *dims, 
 int apply_enqueue(const ApplyReq &q, cudaStream_t st);
 size_t grid_elems(const sc_stencil *s, int bc, const int64_t *dims, bool input);
 int num_sms();
+// Planes per CTA for a streamed launch of `tiles_xy` tiles per plane over
+// `nplanes` planes with halo R, given `slots` = resident CTAs per SM x SMs:
+// minimises ceil(CTAs / slots) * (H + 2R), i.e. whole waves of CTAs that each
+// stream as long a run as the wave count allows.
+int wave_planes(long long tiles_xy, int nplanes, int R, long long slots, int hmin);
 // Testing/tuning knob: fixes the number of output planes per CTA (0 = auto).
 void set_apply_planes_override(int h);
 

@@ -80,3 +80,35 @@ def apply_composed_host(s: Stencil, x: torch.Tensor, y: torch.Tensor, work: torc
                                      ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(work.data_ptr()),
                                      work.numel() * work.element_size(), stream_arg(stream)))
     return y
+
+
+lib.sc_apply_composition_work_bytes.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P]
+lib.sc_apply_composition_work_bytes.restype = ctypes.c_size_t
+lib.sc_apply_composition.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.c_int64,
+                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p]
+lib.sc_apply_composition.restype = ctypes.c_int
+ARITH_NATIVE, ARITH_PAIR = 0, 1
+
+
+def apply_composition_work_bytes(outer: Stencil, inner: Stencil, dtype, bc, dims) -> int:
+    return int(lib.sc_apply_composition_work_bytes(ctypes.byref(outer), ctypes.byref(inner), dtype_code(dtype),
+                                                   bc_code(bc), dims_arg(dims)))
+
+
+def apply_composition(outer: Stencil, inner: Stencil, x: torch.Tensor, y: torch.Tensor, work=None,
+                      bc="periodic", h=(1, 1), dims=None, stream=None, arith="native") -> torch.Tensor:
+    """y = outer(inner(x)): the composed operator in nested form (two passes
+    through a device temporary); arith="pair" evaluates FP64 Laplacian
+    factors in pairs of FP32 numbers."""
+    if dims is None:
+        dims = tuple(reversed(y.shape))
+    nb = apply_composition_work_bytes(outer, inner, y.dtype, bc, dims)
+    if work is None:
+        work = torch.empty(max(nb, 1), dtype=torch.uint8, device=y.device)
+    check(lib.sc_apply_composition(ctypes.byref(outer), ctypes.byref(inner), dtype_code(y.dtype), bc_code(bc),
+                                   dims_arg(dims), int(h[0]), int(h[1]), ctypes.c_void_p(x.data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                   work.numel() * work.element_size(), ARITH_PAIR if arith == "pair" else ARITH_NATIVE,
+                                   stream_arg(stream)))
+    return y

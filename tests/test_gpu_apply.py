@@ -157,3 +157,121 @@ def test_invalid_arguments_are_rejected():
     s1 = sc.stencil_1d(sc.D2_C2)
     with pytest.raises(sc.ScError):
         sc.apply_composed(s1, x, y, bc="periodic", h=(1, 8))
+
+
+COMP_CASES = [(2, 2, (1100, 301)), (2, 4, (1101, 97)), (3, 2, (150, 40, 37)), (3, 4, (67, 19, 23)),
+              (3, 4, (64, 64, 20))]
+
+
+@pytest.mark.parametrize("ndim,order,dims", COMP_CASES)
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("bc", ["periodic", "zero", "ghosted"])
+def test_composition_nested_matches_oracle(ndim, order, dims, dt, bc):
+    """y = B(A x) from the factors (two passes) equals the oracle's apply of
+    the composed stencil, within the rounding bound of the nested sums."""
+    L = sc.laplacian(ndim, order)
+    oL = ost.laplacian(ndim, order)
+    oc = ost.compose(oL, oL)
+    R = oc.radius
+    n = dims[0]
+    w = oracle_weights(oc, Fraction(1, n), np.float64)
+    shape = tuple(reversed(dims))
+    xshape = tuple(s + 2 * R for s in shape) if bc == "ghosted" else shape
+    x = fields.uniform(xshape, seed=zlib.crc32(repr(("nested", ndim, order, dims, bc)).encode()), dtype=dt)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.full(shape, float("nan"), dtype=xt.dtype, device=DEV)
+    sc.apply_composition(L, L, xt, yt, bc=bc, h=(1, n), dims=dims)
+    torch.cuda.synchronize()
+    y_ref = oap.apply(w, x.astype(np.float64), bc, R)
+    absL = ost.Stencil.make({k: abs(v) for k, v in oL.coeffs}, oL.hpow)
+    wabs = ost.fp_weights(ost.compose(absL, absL), Fraction(1, n), np.float64)
+    mag = oap.apply(wabs, np.abs(x.astype(np.float64)), bc, R)
+    eps = np.finfo(dt).eps
+    bound = (2 * oL.npts + 2) * eps * mag
+    if dt == np.float32:
+        bound = bound + oc.npts * np.finfo(np.float32).eps * mag  # float32 weights of each factor
+    err = np.abs(yt.cpu().numpy().astype(np.float64) - y_ref)
+    assert np.all(err <= bound), float(np.max(err / (mag + 1e-300)))
+    if dt == np.float64:
+        assert np.linalg.norm(err) <= 1e-12 * np.linalg.norm(y_ref)
+
+
+def test_star_stencils_use_star_class():
+    """Laplacians (axis points only) in 2D/3D, orders 2/4, all boundaries."""
+    for ndim, order, dims in [(2, 2, (130, 70)), (2, 4, (300, 33)), (3, 2, (40, 30, 20)), (3, 4, (72, 17, 19))]:
+        L = sc.laplacian(ndim, order)
+        oL = ost.laplacian(ndim, order)
+        for dt in (np.float64, np.float32):
+            w = oracle_weights(oL, Fraction(1, dims[0]), dt)
+            for bc in ("periodic", "zero", "ghosted"):
+                shape = tuple(reversed(dims))
+                xs = tuple(s + 2 * oL.radius for s in shape) if bc == "ghosted" else shape
+                x = fields.uniform(xs, seed=11, dtype=dt)
+                yt = torch.empty(shape, dtype=torch.float64 if dt == np.float64 else torch.float32, device=DEV)
+                sc.apply_composed(L, torch.from_numpy(x).to(DEV), yt, bc=bc, h=(1, dims[0]), dims=dims)
+                torch.cuda.synchronize()
+                check(yt.cpu().numpy(), x, w, bc, oL.radius, dt, oL.npts)
+
+
+PAIR_CASES = [(2, 4, (8192, 40)), (2, 2, (1100, 301)), (2, 4, (1101, 97)), (3, 4, (150, 40, 37)),
+              (3, 2, (64, 20, 30)), (3, 4, (68, 33, 17))]
+
+
+def _nested_check(L, oL, x, yt, bc, n, elem_tol):
+    oc = ost.compose(oL, oL)
+    R = oc.radius
+    w = oracle_weights(oc, Fraction(1, n), np.float64)
+    y_ref = oap.apply(w, x, bc, R)
+    absL = ost.Stencil.make({k: abs(v) for k, v in oL.coeffs}, oL.hpow)
+    wabs = ost.fp_weights(ost.compose(absL, absL), Fraction(1, n), np.float64)
+    mag = oap.apply(wabs, np.abs(x), bc, R)
+    err = np.abs(yt.cpu().numpy() - y_ref)
+    assert np.all(err <= elem_tol * mag), float(np.max(err / (mag + 1e-300)))
+    assert np.linalg.norm(err) <= 1e-12 * np.linalg.norm(y_ref)
+
+
+@pytest.mark.parametrize("ndim,order,dims", PAIR_CASES)
+@pytest.mark.parametrize("bc", ["periodic", "zero", "ghosted"])
+def test_pair_arithmetic_fp64_matches_oracle(ndim, order, dims, bc):
+    """FP64 composition evaluated in pairs of FP32 numbers: elementwise
+    within 2^-42 of (|B| o |A|)|x| (a few units of 2^-48 per pass, with room),
+    normwise within the FP64 target 1e-12."""
+    L = sc.laplacian(ndim, order)
+    oL = ost.laplacian(ndim, order)
+    R = 2 * oL.radius
+    n = dims[0]
+    shape = tuple(reversed(dims))
+    xshape = tuple(s + 2 * R for s in shape) if bc == "ghosted" else shape
+    x = fields.uniform(xshape, seed=zlib.crc32(repr(("pair", ndim, order, dims, bc)).encode()))
+    yt = torch.full(shape, float("nan"), dtype=torch.float64, device=DEV)
+    sc.apply_composition(L, L, torch.from_numpy(x).to(DEV), yt, bc=bc, h=(1, n), dims=dims, arith="pair")
+    torch.cuda.synchronize()
+    _nested_check(L, oL, x, yt, bc, n, 2.0 ** -42)
+
+
+def test_pair_arithmetic_out_of_range_inputs_fall_back():
+    """Values that cannot be split into normal floats (tiny, huge, zero mixed
+    in) raise the device flag; the native FP64 passes then recompute y."""
+    dims = (128, 64)
+    L = sc.laplacian(2, 4)
+    oL = ost.laplacian(2, 4)
+    x = fields.uniform((64, 128), seed=3)
+    x[5, 7] = 1e-200
+    x[40, 100] = 1e200
+    x[10, :] = 0.0
+    yt = torch.empty((64, 128), dtype=torch.float64, device=DEV)
+    sc.apply_composition(L, L, torch.from_numpy(x).to(DEV), yt, bc="periodic", h=(1, 128), dims=dims, arith="pair")
+    torch.cuda.synchronize()
+    oc = ost.compose(oL, oL)
+    w = oracle_weights(oc, Fraction(1, 128), np.float64)
+    y_ref = oap.apply(w, x, "periodic", 4)
+    absL = ost.Stencil.make({k: abs(v) for k, v in oL.coeffs}, oL.hpow)
+    wabs = ost.fp_weights(ost.compose(absL, absL), Fraction(1, 128), np.float64)
+    mag = oap.apply(wabs, np.abs(x), "periodic", 4)
+    err = np.abs(yt.cpu().numpy() - y_ref)
+    assert np.all(err <= (2 * oL.npts + 2) * np.finfo(np.float64).eps * mag)
+    # and a field fully in range gives a different (pair) rounding but the same tolerance
+    x2 = fields.uniform((64, 128), seed=4)
+    sc.apply_composition(L, L, torch.from_numpy(x2).to(DEV), yt, bc="periodic", h=(1, 128), dims=dims, arith="pair")
+    torch.cuda.synchronize()
+    _nested_check(L, oL, x2, yt, "periodic", 128, 2.0 ** -42)
