@@ -27,7 +27,8 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
-sys.path.insert(0, ROOT)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
 
@@ -167,44 +168,23 @@ def run_apply_sweep_ours(args, rank, world, local):
                           bytes=_sweep_bytes(n, ndim, dt)))
     torch.cuda.synchronize()
 
-    def run_case(c, ops, how):
-        if how == "flat":
-            sc.apply_composed(ops[c["ndim"]][1], c["x"], c["y"], bc="periodic", h=(1, c["n"]), stream=stream)
-        else:  # nested: outer(inner(x)) from the composition's factors
-            L = ops[c["ndim"]][0]
-            sc.apply_composition(L, L, c["x"], c["y"], work=c["work"], bc="periodic", h=(1, c["n"]),
-                                 stream=stream, arith="pair" if how == "pair" else "native")
-
-    def compose_ops():
-        ops = {}
-        for nd in (2, 3):  # exact host composition is part of every step
-            L = sc.laplacian(nd, 4)
-            ops[nd] = (L, sc.compose_stencil(L, L))
-        return ops
-
-    # autotune: time both evaluation schedules of every case, keep the faster
-    ops = compose_ops()
+    # the library's autotuner times every evaluation schedule x halo-blocking
+    # depth on these arrays and caches the fastest per shape
     tune = {}
     with torch.cuda.stream(stream):
         for c in cases:
-            for how in (("flat", "nested", "pair") if c["dt"] == "f64" else ("flat", "nested")):
-                ts = []
-                for _ in range(3):
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    run_case(c, ops, how)
-                    b.record(stream)
-                    b.synchronize()
-                    ts.append(a.elapsed_time(b))
-                tune.setdefault(c["name"], {})[how] = sorted(ts)[1]
-            c["how"] = min(tune[c["name"]], key=tune[c["name"]].get)
+            L = sc.laplacian(c["ndim"], 4)
+            tune[c["name"]] = sc.autotune_apply(L, L, c["x"], c["y"], c["work"], h=(1, c["n"]), stream=stream)
+            c["how"] = tune[c["name"]]["eval"]
+    torch.cuda.synchronize()
 
     def one_step(record=None):
-        ops = compose_ops()
+        ops = {nd: sc.laplacian(nd, 4) for nd in (2, 3)}  # exact host algebra each step
         for c in cases:
             if record is not None:
                 record[c["name"]][0].record(stream)
-            run_case(c, ops, c["how"])
+            L = ops[c["ndim"]]
+            sc.apply_tuned(L, L, c["x"], c["y"], c["work"], h=(1, c["n"]), stream=stream)
             if record is not None:
                 record[c["name"]][1].record(stream)
 
@@ -236,7 +216,7 @@ def run_apply_sweep_ours(args, rank, world, local):
     for c in cases:
         ms = statistics.mean(ev[c["name"]])
         per_case[c["name"]] = {"ms": ms, "gbs": c["bytes"] / (ms * 1e-3) / 1e9, "bytes": c["bytes"],
-                               "how": c["how"], "tune_ms": tune[c["name"]]}
+                               "how": c["how"], "tune": tune[c["name"]]}
         launches += {"flat": 1, "nested": 2, "pair": 4}[c["how"]] * args.steps
     step_bytes = sum(c["bytes"] for c in cases)
 
@@ -413,17 +393,28 @@ def run_ch(args, local, ndim):
     u = torch.from_numpy(u0).to(dev)
     c = sc.make_ch((n,) * ndim, batch, (1, n), 1e-6, 1.0, eps * eps, prec=args.prec, solver=args.solver,
                    rtol=1e-10)
-    work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
     m0, e0 = sc.ch_stats(c, u)
-    for _ in range(args.warmup):
-        sc.ch_step(c, u, work=work)
-    torch.cuda.synchronize()
-    t, its = [], []
-    for _ in range(args.steps):
+    if args.solver == "persistent":
+        # warm-up steps, then the timed steps replayed from one captured CUDA graph
+        sc.ch_run(c, u, max(args.warmup, 1), use_graph=True)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        infos = sc.ch_step(c, u, work=work)
-        t.append(time.perf_counter() - t0)
-        its.append(max(i["iters"] for i in infos))
+        infos_all = sc.ch_run(c, u, args.steps, use_graph=True)
+        total = time.perf_counter() - t0
+        t = [total / args.steps] * args.steps
+        its = [max(i["iters"] for i in step) for step in infos_all]
+        infos = infos_all[-1]
+    else:
+        work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup):
+            sc.ch_step(c, u, work=work)
+        torch.cuda.synchronize()
+        t, its = [], []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            infos = sc.ch_step(c, u, work=work)
+            t.append(time.perf_counter() - t0)
+            its.append(max(i["iters"] for i in infos))
     m1, e1 = sc.ch_stats(c, u)
     s0 = float(np.abs(u0).sum(axis=tuple(range(1, ndim + 1))).max())
     return {"sec": t, "iters": its, "info": infos[0], "n": n, "batch": batch,
@@ -708,8 +699,7 @@ def main():
                            "l2": "inputs larger than L2 (256 MiB-1 GiB per array), no flush",
                            "per_case_gbs": {k: round(v["gbs"], 1) for k, v in res["per_case"].items()},
                            "per_case_eval": {k: v["how"] for k, v in res["per_case"].items()},
-                           "autotune_ms": {k: {h: round(t, 4) for h, t in v["tune_ms"].items()}
-                                           for k, v in res["per_case"].items()},
+                           "autotuned": {k: v["tune"] for k, v in res["per_case"].items()},
                            "per_case_ms": {k: round(v["ms"], 4) for k, v in res["per_case"].items()},
                            "hbm_frac_per_case": {k: round(v["gbs"] / hbm, 4) for k, v in res["per_case"].items()}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": res["clocks"],

@@ -181,6 +181,42 @@ int sc_apply_composed_host(const sc_stencil *s, int32_t dtype, int32_t bc, const
                            void *work_dev, size_t work_bytes, sc_stream_t stream);
 
 
+
+/* ---- Autotuner -------------------------------------------------------------- */
+
+typedef enum {
+  SC_EVAL_FLAT = 0,   /* sc_apply_composed on compose(outer, inner)           */
+  SC_EVAL_NESTED = 1, /* sc_apply_composition, native arithmetic               */
+  SC_EVAL_PAIR = 2    /* sc_apply_composition, FP32-pair arithmetic (FP64)     */
+} sc_eval;
+
+typedef struct {
+  int32_t eval;    /* sc_eval                                                  */
+  int32_t planes;  /* output planes per CTA (halo-blocking depth; 0 = the
+                      occupancy model)                                         */
+  double ms;       /* measured time of one apply                               */
+} sc_tune_choice;
+
+/* Times every evaluation schedule of the operator compose(outer, inner) --
+ * flat composed weights, nested native, nested FP32-pair (FP64 only) --
+ * crossed with several halo-blocking depths (planes per CTA: the occupancy
+ * model, 16, 32, 64, 128) on the caller's x/y/work and stream (one warm-up
+ * and the median of three runs each; y is overwritten), caches the fastest
+ * for this (shape, dtype, boundary, factors) in the process and returns it.
+ * Blocks until the timing runs finish.  work_bytes >=
+ * sc_apply_composition_work_bytes(outer, inner, ...). */
+int sc_autotune_apply(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                      const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                      void *work_dev, size_t work_bytes, sc_tune_choice *out, sc_stream_t stream);
+/* y = compose(outer, inner) x with the cached choice for this shape (the flat
+ * composed apply with the occupancy model when untuned).  Asynchronous. */
+int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                   const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                   void *work_dev, size_t work_bytes, sc_stream_t stream);
+/* The cached choice for a shape (SC_EINVAL if not tuned). */
+int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                    const int64_t *dims, sc_tune_choice *out);
+
 /* ---- Solvers (device) ------------------------------------------------------ */
 
 typedef enum {
@@ -273,6 +309,18 @@ typedef struct {
 size_t sc_ch_work_bytes(const sc_ch *p);
 int sc_ch_step(const sc_ch *p, double *u_dev, void *work_dev, size_t work_bytes, sc_solve_info *infos,
                sc_stream_t stream);
+
+/* nsteps Cahn-Hilliard steps of every field (the same step as sc_ch_step,
+ * persistent solver), set up once.  With use_graph != 0 one whole step --
+ * right-hand-side kernels, solver-state reset, the cooperative persistent
+ * launch that solves all `batch` fields, and a kernel that records the
+ * step's per-field results in device memory -- is captured once into a CUDA
+ * graph and replayed, with no host synchronisation between steps.
+ * infos[nsteps * batch] receives per-step, per-field results (step-major).
+ * work_bytes >= sc_ch_run_work_bytes(p, nsteps).  Blocking. */
+size_t sc_ch_run_work_bytes(const sc_ch *p, int64_t nsteps);
+int sc_ch_run(const sc_ch *p, double *u_dev, int64_t nsteps, int32_t use_graph, void *work_dev,
+              size_t work_bytes, sc_solve_info *infos, sc_stream_t stream);
 
 /* Mass sum(u) and free energy F(u) = h^d sum[f(u) + kappa/2 sum_a (D+_a u)^2]
  * (forward differences, periodic) of each field, written to host arrays

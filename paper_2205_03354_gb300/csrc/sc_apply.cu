@@ -114,7 +114,7 @@ static int launch_flat(const ApplyReq &q, const T *wts_sparse, cudaStream_t st) 
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
     attr_set = true;
   }
-  g.H = choose_h(kern, K::NTHR, K::SMEM, tiles, ns, R, g_h_override);
+  g.H = choose_h(kern, K::NTHR, K::SMEM, tiles, ns, R, q.planes > 0 ? q.planes : g_h_override);
   const uintptr_t xa = reinterpret_cast<uintptr_t>(q.x), ya = reinterpret_cast<uintptr_t>(q.y);
   bool vec = (xa % 16 == 0) && (ya % 16 == 0) && (g.nx % K::CH == 0);
   if (q.bc == SC_BC_GHOSTED) vec = vec && (q.s->radius == R) && ((R - K::HX) % K::CH == 0) &&
@@ -235,7 +235,7 @@ size_t composition_work_bytes(const sc_stencil *B, const sc_stencil *A, int dtyp
 // temporary, then the outer stencil (Eq. C=B(A), nested form).
 int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims,
                         int64_t h_num, int64_t h_den, const void *x, void *y, void *work, cudaStream_t st,
-                        int arith) {
+                        int arith, int planes) {
   const int nd = A->ndim, rA = A->radius, rB = B->radius;
   const size_t es = dtype == SC_F64 ? 8 : 4;
   char *w = static_cast<char *>(work);
@@ -269,12 +269,13 @@ int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int
   }
   if (bc == SC_BC_PERIODIC) {
     if (pair) {
-      if (int rc = df_composition_enqueue(nd, rA, x, t, y, dims, dims, SC_BC_PERIODIC, ca, cb, scale, flag, st))
+      if (int rc = df_composition_enqueue(nd, rA, x, t, y, dims, dims, SC_BC_PERIODIC, ca, cb, scale, flag, st,
+                                          planes))
         return rc;
     }
-    ApplyReq qa{A, dtype, SC_BC_PERIODIC, dims, h_num, h_den, x, t, pair ? flag : nullptr};
+    ApplyReq qa{A, dtype, SC_BC_PERIODIC, dims, h_num, h_den, x, t, pair ? flag : nullptr, pair ? 0 : planes};
     if (int rc = apply_enqueue(qa, st)) return rc;
-    ApplyReq qb{B, dtype, SC_BC_PERIODIC, dims, h_num, h_den, t, y, pair ? flag : nullptr};
+    ApplyReq qb{B, dtype, SC_BC_PERIODIC, dims, h_num, h_den, t, y, pair ? flag : nullptr, pair ? 0 : planes};
     return apply_enqueue(qb, st);
   }
   const void *xin = x;
@@ -292,12 +293,13 @@ int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int
   }
   // x (n + 2(rA + rB)) -> t (n + 2 rB) -> y (n)
   if (pair) {
-    if (int rc = df_composition_enqueue(nd, rA, xin, t, y, dext, dims, SC_BC_GHOSTED, ca, cb, scale, flag, st))
+    if (int rc = df_composition_enqueue(nd, rA, xin, t, y, dext, dims, SC_BC_GHOSTED, ca, cb, scale, flag, st,
+                                        planes))
       return rc;
   }
-  ApplyReq qa{A, dtype, SC_BC_GHOSTED, dext, h_num, h_den, xin, t, pair ? flag : nullptr};
+  ApplyReq qa{A, dtype, SC_BC_GHOSTED, dext, h_num, h_den, xin, t, pair ? flag : nullptr, pair ? 0 : planes};
   if (int rc = apply_enqueue(qa, st)) return rc;
-  ApplyReq qb{B, dtype, SC_BC_GHOSTED, dims, h_num, h_den, t, y, pair ? flag : nullptr};
+  ApplyReq qb{B, dtype, SC_BC_GHOSTED, dims, h_num, h_den, t, y, pair ? flag : nullptr, pair ? 0 : planes};
   return apply_enqueue(qb, st);
 }
 

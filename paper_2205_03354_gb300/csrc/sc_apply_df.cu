@@ -327,7 +327,7 @@ bool star_int_form(const sc_stencil *s, float *c0, float *c1, float *c2) {
 
 template <int NDIM, int R, bool IN_PAIR, bool OUT_PAIR>
 static int launch_df(const void *x, void *y, const int64_t *dims, int bc, float c0, float c1, float c2,
-                     double scale, int *flag, cudaStream_t st) {
+                     double scale, int *flag, cudaStream_t st, int planes) {
   using K = DfPass<NDIM, R, IN_PAIR, OUT_PAIR>;
   DfGeom g;
   std::memset(&g, 0, sizeof(g));
@@ -361,7 +361,8 @@ static int launch_df(const void *x, void *y, const int64_t *dims, int bc, float 
   }
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, K::NTHR, K::SMEM);
-  g.H = wave_planes(txy, ns, R, (long long)std::max(occ, 1) * num_sms(), std::max(4 * R, 8));
+  g.H = planes > 0 ? std::min(planes, ns)
+                   : wave_planes(txy, ns, R, (long long)std::max(occ, 1) * num_sms(), std::max(4 * R, 8));
   dim3 grid((g.nx + K::BX - 1) / K::BX, NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : (ns + g.H - 1) / g.H,
             NDIM == 3 ? (ns + g.H - 1) / g.H : 1);
   kern<<<grid, K::NTHR, K::SMEM, st>>>(x, y, g, flag);
@@ -372,19 +373,20 @@ static int launch_df(const void *x, void *y, const int64_t *dims, int bc, float 
 
 template <int NDIM, int R>
 static int df_two_passes(const void *x, void *t, void *y, const int64_t *dims_t, const int64_t *dims_y, int bc,
-                         const float *ca, const float *cb, double scale, int *flag, cudaStream_t st) {
-  if (int rc = launch_df<NDIM, R, false, true>(x, t, dims_t, bc, ca[0], ca[1], ca[2], 1.0, flag, st)) return rc;
-  return launch_df<NDIM, R, true, false>(t, y, dims_y, bc, cb[0], cb[1], cb[2], scale, flag, st);
+                         const float *ca, const float *cb, double scale, int *flag, cudaStream_t st, int planes) {
+  if (int rc = launch_df<NDIM, R, false, true>(x, t, dims_t, bc, ca[0], ca[1], ca[2], 1.0, flag, st, planes))
+    return rc;
+  return launch_df<NDIM, R, true, false>(t, y, dims_y, bc, cb[0], cb[1], cb[2], scale, flag, st, planes);
 }
 
 int df_composition_enqueue(int ndim, int R, const void *x, void *t, void *y, const int64_t *dims_t,
                            const int64_t *dims_y, int bc, const float *ca, const float *cb, double scale,
-                           int *flag, cudaStream_t st) {
+                           int *flag, cudaStream_t st, int planes) {
   if (ndim == 2)
-    return R == 1 ? df_two_passes<2, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st)
-                  : df_two_passes<2, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st);
-  return R == 1 ? df_two_passes<3, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st)
-                : df_two_passes<3, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st);
+    return R == 1 ? df_two_passes<2, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes)
+                  : df_two_passes<2, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes);
+  return R == 1 ? df_two_passes<3, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes)
+                : df_two_passes<3, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes);
 }
 
 }  // namespace sc

@@ -17,6 +17,6 @@ bool star_int_form(const sc_stencil *s, float *c0, float *c1, float *c2);
 // when an input value cannot be split into normal floats.
 int df_composition_enqueue(int ndim, int R, const void *x, void *t, void *y, const int64_t *dims_t,
                            const int64_t *dims_y, int bc, const float *ca, const float *cb, double scale,
-                           int *flag, cudaStream_t st);
+                           int *flag, cudaStream_t st, int planes = 0);
 
 }  // namespace sc

@@ -18,7 +18,13 @@ struct ApplyReq {
   const void *x;
   void *y;
   const int *guard = nullptr;  // if set: the kernel only works when *guard != 0
+  int planes = 0;              // output planes per CTA (0: occupancy model)
 };
+
+size_t composition_work_bytes(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims);
+int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims,
+                        int64_t h_num, int64_t h_den, const void *x, void *y, void *work, cudaStream_t st,
+                        int arith, int planes = 0);
 
 int validate_apply(const sc_stencil *s, int dtype, int bc, const int64_t *dims, int64_t h_num,
                    int64_t h_den);

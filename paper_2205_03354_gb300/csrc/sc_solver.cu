@@ -348,23 +348,10 @@ static int setup_ch(const sc_ch *cp, const ProbSpec &sp, SolveProb &P, const Pro
 
 // Assigns CTA groups for problems[first..last) and launches one cooperative
 // persistent kernel for them.
-template <typename TI>
-static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx, SolveProb *dprobs,
-                        int *dmap, unsigned *dbars, cudaStream_t st, long long budget,
-                        double slice_ms) {
-  auto kern = cg_persistent_kernel<TI, 2>;
-  const size_t smem = smem_bytes_cg();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr = true;
-  }
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, CG_NTHR, smem);
-  if (nb < 1) return fail(SC_ECUDA, "persistent CG kernel does not fit on an SM");
-  const int G = nb * num_sms();
-  // proportional split of the CTAs by problem size, at least one each,
-  // at most the problem's number of work units
+// CTA groups for problems hp[idx]: proportional to size, at least one each,
+// at most the problem's number of work units; returns the CTA -> problem map.
+static int assign_groups(std::vector<SolveProb> &hp, const std::vector<int> &idx, int G, unsigned *dbars,
+                         std::vector<int> &map) {
   double wsum = 0.0;
   for (int i : idx) wsum += double(hp[i].npts);
   int used = 0;
@@ -378,7 +365,7 @@ static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx,
     used += c;
   }
   if (used > G) return fail(SC_EINVAL, "internal: CTA assignment exceeds the grid");
-  std::vector<int> map(used, -1);
+  map.assign(used, -1);
   int c0 = 0;
   for (size_t k = 0; k < idx.size(); ++k) {
     SolveProb &P = hp[idx[k]];
@@ -388,18 +375,65 @@ static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx,
     for (int j = 0; j < nc[k]; ++j) map[c0 + j] = idx[k];
     c0 += nc[k];
   }
+  return SC_OK;
+}
+
+template <typename TI>
+static size_t cg_smem_setup() {
+  auto kern = cg_persistent_kernel<TI, 2>;
+  const size_t smem = smem_bytes_cg();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    attr = true;
+  }
+  return smem;
+}
+
+// Cooperative launch of the persistent kernel over descriptors already on
+// the device (capturable in a CUDA graph).
+template <typename TI>
+static int enqueue_cg(const SolveProb *dprobs, const int *dmap, int grid, cudaStream_t st, long long budget,
+                      unsigned long long slice_ns) {
+  auto kern = cg_persistent_kernel<TI, 2>;
+  const size_t smem = cg_smem_setup<TI>();
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(CG_NTHR);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, dprobs, dmap, budget, slice_ns);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "cooperative launch: %s", cudaGetErrorString(e));
+  return SC_OK;
+}
+
+// Assigns CTA groups for problems hp[idx] and launches one cooperative
+// persistent kernel for them (synchronous).
+template <typename TI>
+static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx, SolveProb *dprobs,
+                        int *dmap, unsigned *dbars, cudaStream_t st, long long budget,
+                        double slice_ms) {
+  auto kern = cg_persistent_kernel<TI, 2>;
+  const size_t smem = cg_smem_setup<TI>();
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, CG_NTHR, smem);
+  if (nb < 1) return fail(SC_ECUDA, "persistent CG kernel does not fit on an SM");
+  const int G = nb * num_sms();
+  std::vector<int> map;
+  if (int rc = assign_groups(hp, idx, G, dbars, map)) return rc;
   cudaMemcpyAsync(dprobs, hp.data(), hp.size() * sizeof(SolveProb), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(dbars, 0, hp.size() * 2 * sizeof(unsigned), st);
-  const SolveProb *a0 = dprobs;
-  const int *a1 = dmap;
-  long long a2 = budget;
-  unsigned long long a3 = slice_ms > 0.0 ? (unsigned long long)(slice_ms * 1e6) : 0ull;
-  void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2, (void *)&a3};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(used), dim3(CG_NTHR), args, smem, st);
-  if (e != cudaSuccess) return fail(SC_ECUDA, "cooperative launch: %s", cudaGetErrorString(e));
+  const unsigned long long slice_ns = slice_ms > 0.0 ? (unsigned long long)(slice_ms * 1e6) : 0ull;
+  if (int rc = enqueue_cg<TI>(dprobs, dmap, int(map.size()), st, budget, slice_ns)) return rc;
   // pageable sources above: finish before the vectors go out of scope
-  e = cudaStreamSynchronize(st);
+  cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(SC_ECUDA, "persistent CG: %s", cudaGetErrorString(e));
   return SC_OK;
 }
@@ -713,11 +747,157 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
   return SC_OK;
 }
 
+// Resets every problem's solver state (a graph node in the multi-step run).
+__global__ void k_reset_states(const SolveProb *__restrict__ probs, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    SolveState *s = probs[i].st;
+    s->iters = 0;
+    s->outer = 0;
+    s->rr = 0.0;
+    s->rmax = 0.0;
+    s->bnorm = 0.0;
+    s->rel = 0.0;
+    s->sumb = 0.0;
+    s->status = 0;
+    s->phase = 0;
+    s->beta = 0.0;
+  }
+}
+
+// Appends every problem's final state of this step to out[step * n + i].
+__global__ void k_record_states(const SolveProb *__restrict__ probs, int n, SolveState *__restrict__ out,
+                                int *__restrict__ step) {
+  const int i = threadIdx.x;
+  const int k = *step;
+  for (int j = i; j < n; j += blockDim.x) out[(long long)k * n + j] = *probs[j].st;
+  __syncthreads();
+  if (i == 0) *step = k + 1;
+}
+
 }  // namespace sc
 
 using namespace sc;
 
 extern "C" {
+
+size_t sc_ch_run_work_bytes(const sc_ch *c, int64_t nsteps) {
+  if (ch_validate(c) || nsteps < 1) return 0;
+  const size_t base = sc_ch_work_bytes(c);
+  return base + size_t(nsteps) * c->batch * sizeof(SolveState) + 1024;
+}
+
+int sc_ch_run(const sc_ch *c, double *u_dev, int64_t nsteps, int32_t use_graph, void *work_dev,
+              size_t work_bytes, sc_solve_info *infos, sc_stream_t stream) {
+  if (int rc = ch_validate(c)) return rc;
+  if (!u_dev || !infos || !work_dev || nsteps < 1) return fail(SC_EINVAL, "bad argument");
+  if (c->solver != SC_SOLVER_PERSISTENT) return fail(SC_EINVAL, "sc_ch_run uses the persistent solver");
+  const size_t need = sc_ch_run_work_bytes(c, nsteps);
+  if (work_bytes < need) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, need);
+  auto t0 = std::chrono::steady_clock::now();
+  // The run goes on a private non-blocking stream ordered after the caller's
+  // (the legacy default stream cannot be captured into a graph).
+  cudaStream_t cst = (cudaStream_t)stream, st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(SC_ECUDA, "stream creation failed");
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } guard{st};
+  {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, cst);
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+  }
+  std::vector<ProbSpec> sps(c->batch);
+  for (int i = 0; i < c->batch; ++i) ch_spec(c, i, u_dev, sps[i]);
+  Carver cv(work_dev, work_bytes);
+  std::vector<SolveProb> hp(sps.size());
+  std::vector<ProbAux> aux(sps.size());
+  for (size_t i = 0; i < sps.size(); ++i) {
+    layout(sps[i], cv, hp[i], aux[i]);
+    aux[i].ones = static_cast<double *>(cv.take(std::max<long long>(hp[i].npts, 1) * 8));
+  }
+  SolveProb *dprobs = static_cast<SolveProb *>(cv.take(sps.size() * sizeof(SolveProb)));
+  int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(8) * 1024 * 16));
+  unsigned *dbars = static_cast<unsigned *>(cv.take(sps.size() * 2 * sizeof(unsigned)));
+  SolveState *dinfo = static_cast<SolveState *>(cv.take(size_t(nsteps) * sps.size() * sizeof(SolveState)));
+  int *dstep = static_cast<int *>(cv.take(sizeof(int)));
+  for (size_t i = 0; i < sps.size(); ++i)
+    if (int rc = upload_prob(sps[i], hp[i], aux[i], st)) return rc;
+  const bool mixed = hp[0].mixed != 0;
+  const int G = max_group_ctas(mixed);
+  std::vector<int> idx(sps.size()), map;
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = int(i);
+  if (int rc = assign_groups(hp, idx, G, dbars, map)) return rc;
+  cudaMemcpyAsync(dprobs, hp.data(), hp.size() * sizeof(SolveProb), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(dstep, 0, sizeof(int), st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "set-up: %s", cudaGetErrorString(e));
+  const int n = int(sps.size());
+  auto enqueue_step = [&]() -> int {
+    for (int i = 0; i < n; ++i)
+      if (int rc = setup_ch(c, sps[i], hp[i], aux[i], st)) return rc;
+    k_reset_states<<<(n + 127) / 128, 128, 0, st>>>(dprobs, n);
+    cudaMemsetAsync(dbars, 0, size_t(n) * 2 * sizeof(unsigned), st);
+    int rc = mixed ? enqueue_cg<float>(dprobs, dmap, int(map.size()), st, LLONG_MAX, 0ull)
+                   : enqueue_cg<double>(dprobs, dmap, int(map.size()), st, LLONG_MAX, 0ull);
+    if (rc) return rc;
+    k_record_states<<<1, 128, 0, st>>>(dprobs, n, dinfo, dstep);
+    return SC_OK;
+  };
+  // first step directly (also initialises every kernel's attributes)
+  if (int rc = enqueue_step()) return rc;
+  if (nsteps > 1) {
+    if (use_graph) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) return fail(SC_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+      int rc = enqueue_step();
+      e = cudaStreamEndCapture(st, &graph);
+      if (rc) return rc;
+      if (e != cudaSuccess) return fail(SC_ECUDA, "end capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(SC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      }
+      for (int64_t k = 1; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, st);
+      cudaError_t e2 = cudaStreamSynchronize(st);
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(SC_ECUDA, "graph replay: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    } else {
+      for (int64_t k = 1; k < nsteps; ++k)
+        if (int rc = enqueue_step()) return rc;
+    }
+  }
+  std::vector<SolveState> hs(size_t(nsteps) * n);
+  cudaMemcpyAsync(hs.data(), dinfo, hs.size() * sizeof(SolveState), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "multi-step run: %s", cudaGetErrorString(e));
+  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (size_t k = 0; k < hs.size(); ++k) {
+    sc_solve_info &in = infos[k];
+    std::memset(&in, 0, sizeof(in));
+    in.prec = mixed ? SC_PREC_MIXED : SC_PREC_F64;
+    in.seconds = sec;
+    in.iters = hs[k].iters;
+    in.outer = hs[k].outer;
+    in.rel_res = hs[k].rel;
+    in.status = hs[k].phase == 2 ? hs[k].status : SC_ETIMEOUT;
+  }
+  clear_error();
+  return SC_OK;
+}
 
 size_t sc_bvp_batch_work_bytes(const sc_bvp *probs, int32_t count) {
   if (!probs || count < 1) return 0;

@@ -1,0 +1,175 @@
+// Autotuner of the composed-stencil apply: evaluation schedule (flat
+// composed weights, nested native B(A x), nested FP32-pair for FP64
+// Laplacian factors) and halo-blocking depth (output planes per CTA, which
+// sets how often the 2R halo planes are re-read), timed on the caller's data
+// and stream; the winner is cached per problem shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "sc_apply_host.h"
+#include "sc_internal.h"
+
+namespace sc {
+
+typedef std::tuple<int, int, int, long long, long long, long long, long long, long long> TuneKey;
+
+static std::mutex g_tune_mu;
+static std::map<TuneKey, sc_tune_choice> g_tune;
+
+static long long fingerprint(const sc_stencil *s) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](long long v) {
+    h ^= (unsigned long long)v;
+    h *= 1099511628211ull;
+  };
+  mix(s->ndim);
+  mix(s->npts);
+  mix(s->hpow);
+  mix(s->den);
+  for (int k = 0; k < s->npts; ++k) {
+    mix(s->off[k][0]);
+    mix(s->off[k][1]);
+    mix(s->off[k][2]);
+    mix(s->num[k]);
+  }
+  return (long long)h;
+}
+
+static TuneKey key_of(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims) {
+  return TuneKey(A->ndim, dtype, bc, dims[0], dims[1], A->ndim == 3 ? dims[2] : 1, fingerprint(B),
+                 fingerprint(A));
+}
+
+static int run_choice(const sc_stencil *B, const sc_stencil *A, const sc_stencil *C, int dtype, int bc,
+                      const int64_t *dims, int64_t hn, int64_t hd, const void *x, void *y, void *work,
+                      const sc_tune_choice &c, cudaStream_t st) {
+  if (c.eval == SC_EVAL_FLAT) {
+    ApplyReq q{C, dtype, bc, dims, hn, hd, x, y, nullptr, c.planes};
+    return apply_enqueue(q, st);
+  }
+  return composition_enqueue(B, A, dtype, bc, dims, hn, hd, x, y, work, st,
+                             c.eval == SC_EVAL_PAIR ? SC_ARITH_PAIR : SC_ARITH_NATIVE, c.planes);
+}
+
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+int sc_autotune_apply(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                      const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                      void *work_dev, size_t work_bytes, sc_tune_choice *out, sc_stream_t stream) {
+  if (int rc = validate_apply(outer, dtype, bc, dims, h_num, h_den)) return rc;
+  if (int rc = validate_apply(inner, dtype, bc, dims, h_num, h_den)) return rc;
+  if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
+  if (!x_dev || !y_dev || !work_dev || x_dev == y_dev) return fail(SC_EINVAL, "bad device pointers");
+  if (work_bytes < composition_work_bytes(outer, inner, dtype, bc, dims))
+    return fail(SC_ENOMEM, "work space too small");
+  sc_stencil C;
+  if (int rc = sc_compose_stencil(outer, inner, &C)) return rc;
+  if (C.radius > SC_MAX_APPLY_RADIUS) return fail(SC_EINVAL, "composed radius too large");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nd = outer->ndim;
+  const int nplanes = int(nd == 3 ? dims[2] : dims[1]);
+  std::vector<sc_tune_choice> cands;
+  const int evals[3] = {SC_EVAL_FLAT, SC_EVAL_NESTED, SC_EVAL_PAIR};
+  for (int e : evals) {
+    if (e == SC_EVAL_PAIR && dtype != SC_F64) continue;
+    // planes per CTA: the occupancy model (0) and a spread of fixed depths
+    const int ps[5] = {0, 16, 32, 64, 128};
+    for (int p : ps) {
+      if (p > nplanes) continue;
+      sc_tune_choice c;
+      std::memset(&c, 0, sizeof(c));
+      c.eval = e;
+      c.planes = p;
+      cands.push_back(c);
+    }
+  }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  sc_tune_choice best;
+  std::memset(&best, 0, sizeof(best));
+  best.ms = 1e300;
+  for (sc_tune_choice &c : cands) {
+    // one warm-up, then the median of three timed runs
+    int rc = run_choice(outer, inner, &C, dtype, bc, dims, h_num, h_den, x_dev, y_dev, work_dev, c, st);
+    if (rc) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return rc;
+    }
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(a, st);
+      run_choice(outer, inner, &C, dtype, bc, dims, h_num, h_den, x_dev, y_dev, work_dev, c, st);
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(&t[r], a, b);
+    }
+    std::sort(t, t + 3);
+    c.ms = t[1];
+    if (c.ms < best.ms) best = c;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SC_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key_of(outer, inner, dtype, bc, dims)] = best;
+  }
+  if (out) *out = best;
+  clear_error();
+  return SC_OK;
+}
+
+int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                   const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,
+                   void *work_dev, size_t work_bytes, sc_stream_t stream) {
+  if (int rc = validate_apply(outer, dtype, bc, dims, h_num, h_den)) return rc;
+  if (int rc = validate_apply(inner, dtype, bc, dims, h_num, h_den)) return rc;
+  if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
+  if (!x_dev || !y_dev || x_dev == y_dev) return fail(SC_EINVAL, "bad device pointers");
+  sc_tune_choice c;
+  std::memset(&c, 0, sizeof(c));
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key_of(outer, inner, dtype, bc, dims));
+    if (it != g_tune.end()) {
+      c = it->second;
+      have = true;
+    }
+  }
+  if (!have) c.eval = SC_EVAL_FLAT;  // untuned: the composed weights, model depth
+  if (c.eval != SC_EVAL_FLAT && (!work_dev || work_bytes < composition_work_bytes(outer, inner, dtype, bc, dims)))
+    return fail(SC_ENOMEM, "work space too small for the tuned schedule");
+  sc_stencil C;
+  if (int rc = sc_compose_stencil(outer, inner, &C)) return rc;
+  int rc = run_choice(outer, inner, &C, dtype, bc, dims, h_num, h_den, x_dev, y_dev, work_dev, c,
+                      (cudaStream_t)stream);
+  if (!rc) clear_error();
+  return rc;
+}
+
+int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                    const int64_t *dims, sc_tune_choice *out) {
+  if (!outer || !inner || !dims || !out) return fail(SC_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key_of(outer, inner, dtype, bc, dims));
+  if (it == g_tune.end()) return fail(SC_EINVAL, "shape not tuned");
+  *out = it->second;
+  clear_error();
+  return SC_OK;
+}
+
+}  // extern "C"

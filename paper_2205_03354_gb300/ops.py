@@ -112,3 +112,47 @@ def apply_composition(outer: Stencil, inner: Stencil, x: torch.Tensor, y: torch.
                                    work.numel() * work.element_size(), ARITH_PAIR if arith == "pair" else ARITH_NATIVE,
                                    stream_arg(stream)))
     return y
+
+
+EVAL_NAMES = {0: "flat", 1: "nested", 2: "pair"}
+
+
+class TuneChoice(ctypes.Structure):
+    _fields_ = [("eval", ctypes.c_int32), ("planes", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"eval": EVAL_NAMES[self.eval], "planes": int(self.planes), "ms": float(self.ms)}
+
+
+_TUNE_ARGS = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+lib.sc_autotune_apply.argtypes = _TUNE_ARGS + [ctypes.POINTER(TuneChoice), ctypes.c_void_p]
+lib.sc_autotune_apply.restype = ctypes.c_int
+lib.sc_apply_tuned.argtypes = _TUNE_ARGS + [ctypes.c_void_p]
+lib.sc_apply_tuned.restype = ctypes.c_int
+lib.sc_tuned_choice.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.POINTER(TuneChoice)]
+lib.sc_tuned_choice.restype = ctypes.c_int
+
+
+def _tune_args(outer, inner, x, y, work, bc, h, dims):
+    if dims is None:
+        dims = tuple(reversed(y.shape))
+    return (ctypes.byref(outer), ctypes.byref(inner), dtype_code(y.dtype), bc_code(bc), dims_arg(dims),
+            int(h[0]), int(h[1]), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+            ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size())
+
+
+def autotune_apply(outer: Stencil, inner: Stencil, x, y, work, bc="periodic", h=(1, 1), dims=None,
+                   stream=None) -> dict:
+    """Times the evaluation schedules x halo-blocking depths and caches the
+    fastest for this shape (y is overwritten)."""
+    c = TuneChoice()
+    check(lib.sc_autotune_apply(*_tune_args(outer, inner, x, y, work, bc, h, dims), ctypes.byref(c),
+                                stream_arg(stream)))
+    return c.as_dict()
+
+
+def apply_tuned(outer: Stencil, inner: Stencil, x, y, work, bc="periodic", h=(1, 1), dims=None, stream=None):
+    """y = compose(outer, inner) x with the tuned schedule for this shape."""
+    check(lib.sc_apply_tuned(*_tune_args(outer, inner, x, y, work, bc, h, dims), stream_arg(stream)))
+    return y

@@ -180,3 +180,22 @@ def ch_stats_noalloc(c: Ch, u: torch.Tensor, stream=None):
     e = (ctypes.c_double * c.batch)()
     check(lib.sc_ch_stats_noalloc(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), m, e, stream_arg(stream)))
     return list(m), list(e)
+
+
+lib.sc_ch_run_work_bytes.argtypes = [_CP, ctypes.c_int64]
+lib.sc_ch_run_work_bytes.restype = ctypes.c_size_t
+lib.sc_ch_run.argtypes = [_CP, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                          _IP, ctypes.c_void_p]
+lib.sc_ch_run.restype = ctypes.c_int
+
+
+def ch_run(c: Ch, u: torch.Tensor, nsteps: int, use_graph=True, work=None, stream=None) -> list:
+    """nsteps IMEX steps of every field of u in place; returns per-step lists
+    of per-field info dicts."""
+    nb = int(lib.sc_ch_run_work_bytes(ctypes.byref(c), nsteps))
+    w = _work(nb, u.device, work)
+    infos = (SolveInfo * (nsteps * c.batch))()
+    check(lib.sc_ch_run(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), nsteps, 1 if use_graph else 0,
+                        ctypes.c_void_p(w.data_ptr()), nb, infos, stream_arg(stream)))
+    d = [i.as_dict() for i in infos]
+    return [d[k * c.batch:(k + 1) * c.batch] for k in range(nsteps)]

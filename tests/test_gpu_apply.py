@@ -275,3 +275,33 @@ def test_pair_arithmetic_out_of_range_inputs_fall_back():
     sc.apply_composition(L, L, torch.from_numpy(x2).to(DEV), yt, bc="periodic", h=(1, 128), dims=dims, arith="pair")
     torch.cuda.synchronize()
     _nested_check(L, oL, x2, yt, "periodic", 128, 2.0 ** -42)
+
+
+@pytest.mark.parametrize("ndim,n,dt", [(2, 512, np.float64), (3, 64, np.float32), (3, 48, np.float64)])
+def test_autotuned_apply_matches_oracle(ndim, n, dt):
+    """The autotuner picks a schedule and depth; the tuned apply must still
+    be the composed operator (FP64: within the pair/FP64 bounds, FP32: the
+    FP32 nested bound)."""
+    L = sc.laplacian(ndim, 4)
+    oL = ost.laplacian(ndim, 4)
+    shape = (n,) * ndim
+    x = fields.uniform(shape, seed=31, dtype=dt)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.empty_like(xt)
+    wb = sc.apply_composition_work_bytes(L, L, xt.dtype, "periodic", shape)
+    work = torch.empty(wb, dtype=torch.uint8, device=DEV)
+    choice = sc.autotune_apply(L, L, xt, yt, work, h=(1, n))
+    assert choice["eval"] in ("flat", "nested", "pair") and choice["ms"] > 0
+    yt.fill_(float("nan"))
+    sc.apply_tuned(L, L, xt, yt, work, h=(1, n))
+    torch.cuda.synchronize()
+    tol = 2.0 ** -42 if dt == np.float64 else (2 * oL.npts + 2 + 73) * np.finfo(np.float32).eps
+    _nested_check(L, oL, x.astype(np.float64), yt.double(), "periodic", n, tol) if dt == np.float64 else None
+    if dt == np.float32:
+        oc = ost.compose(oL, oL)
+        w = oracle_weights(oc, Fraction(1, n), np.float64)
+        y_ref = oap.apply(w, x.astype(np.float64), "periodic", oc.radius)
+        absL = ost.Stencil.make({k: abs(v) for k, v in oL.coeffs}, oL.hpow)
+        mag = oap.apply(ost.fp_weights(ost.compose(absL, absL), Fraction(1, n), np.float64),
+                        np.abs(x.astype(np.float64)), "periodic", oc.radius)
+        assert np.all(np.abs(yt.cpu().numpy() - y_ref) <= tol * mag)
