@@ -40,12 +40,14 @@ int num_sms() {
 }
 
 int wave_planes(long long tiles_xy, int nplanes, int R, long long slots, int hmin) {
-  // The kernels are throughput-bound per SM: the run time follows the
-  // busiest SM's work, ceil(CTAs / SMs) * (H + 2R).  Candidates must fill
-  // every resident slot at least once (else SMs idle); small grids that
-  // cannot take the smallest H.
+  // Each SM runs up to occ = slots / SMs CTAs at a time; a CTA streams H + 2R
+  // planes.  Time ~ rounds * (H + 2R) with rounds = ceil(ceil(CTAs/SMs)/occ):
+  // a last round with a single CTA per SM costs as much as a full one.
+  // Grids that leave more than a quarter of the slots empty are only taken
+  // when nothing larger exists (small problems).
   if (nplanes <= 1) return 1;
   const long long sms = num_sms();
+  const long long occ = std::max<long long>(1, slots / sms);
   long long best_h = -1, small_h = nplanes;
   double best = 1e300;
   for (long long zb = 1; zb <= nplanes; ++zb) {
@@ -53,8 +55,10 @@ int wave_planes(long long tiles_xy, int nplanes, int R, long long slots, int hmi
     if (h < hmin && zb > 1) break;
     small_h = h;
     const long long ctas = tiles_xy * ((nplanes + h - 1) / h);
-    if (ctas >= slots) {
-      const double cost = double((ctas + sms - 1) / sms) * double(h + 2 * R);
+    if (4 * ctas >= 3 * slots) {
+      const long long per_sm = (ctas + sms - 1) / sms;
+      const long long rounds = (per_sm + occ - 1) / occ;
+      const double cost = double(rounds) * double(h + 2 * R);
       if (cost < best * 0.999) {
         best = cost;
         best_h = h;

@@ -47,23 +47,34 @@ struct BoxWeights {
   T w[N];
 };
 
-// Tile shape per (dtype, ndim); VX * sizeof(T) = 16 bytes.
-template <typename T, int NDIM>
+// Tile shape per (dtype, ndim, family); VX * sizeof(T) is a multiple of 16
+// bytes.  Family 0: standalone streaming applies; family 1: the solver's
+// tiles.  They are the same today (8 outputs per thread in 2D measured slower
+// than 4); the split lets the two be tuned separately.
+template <typename T, int NDIM, int FAM>
 struct TileCfg;
 template <>
-struct TileCfg<float, 2> {
+struct TileCfg<float, 2, 0> {
   static constexpr int VX = 4, VY = 1, TX = 128, TY = 1;
 };
 template <>
-struct TileCfg<double, 2> {
+struct TileCfg<double, 2, 0> {
   static constexpr int VX = 2, VY = 1, TX = 128, TY = 1;
 };
 template <>
-struct TileCfg<float, 3> {
-  static constexpr int VX = 4, VY = 2, TX = 16, TY = 8;
+struct TileCfg<float, 2, 1> {
+  static constexpr int VX = 4, VY = 1, TX = 128, TY = 1;
 };
 template <>
-struct TileCfg<double, 3> {
+struct TileCfg<double, 2, 1> {
+  static constexpr int VX = 2, VY = 1, TX = 128, TY = 1;
+};
+template <int FAM>
+struct TileCfg<float, 3, FAM> {
+  static constexpr int VX = 4, VY = 2, TX = 16, TY = 8;
+};
+template <int FAM>
+struct TileCfg<double, 3, FAM> {
   static constexpr int VX = 2, VY = 2, TX = 32, TY = 4;
 };
 
@@ -78,9 +89,9 @@ struct ApplyGeom {
   long long out_ss;   // output plane stride (3D)
 };
 
-template <typename T, int NDIM, int R, int CLS>
+template <typename T, int NDIM, int R, int CLS, int FAM = 0>
 struct FlatApply {
-  using Cfg = TileCfg<T, NDIM>;
+  using Cfg = TileCfg<T, NDIM, FAM>;
   static constexpr int VX = Cfg::VX, VY = Cfg::VY, TX = Cfg::TX, TY = Cfg::TY;
   static constexpr int NTHR = TX * TY;
   static constexpr int BX = TX * VX;
@@ -257,12 +268,15 @@ struct StoreEpi {
   __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX]) const {
     T *dst = y + (long long)j * (NDIM == 3 ? g->out_ss : g->out_sy) +
              (NDIM == 3 ? (long long)yy * g->out_sy : 0) + xo;
-    if (g->vec && xo + VX <= g->nx && sizeof(T) * VX == 16) {
-      if (sizeof(T) == 4) {
-        *reinterpret_cast<float4 *>(dst) =
-            make_float4(float(v[0]), float(v[1 % VX]), float(v[2 % VX]), float(v[3 % VX]));
-      } else {
-        *reinterpret_cast<double2 *>(dst) = make_double2(double(v[0]), double(v[1 % VX]));
+    if (g->vec && xo + VX <= g->nx && (sizeof(T) * VX) % 16 == 0) {
+#pragma unroll
+      for (int c = 0; c < VX; c += 16 / int(sizeof(T))) {
+        if (sizeof(T) == 4) {
+          *reinterpret_cast<float4 *>(dst + c) = make_float4(float(v[c]), float(v[(c + 1) % VX]),
+                                                              float(v[(c + 2) % VX]), float(v[(c + 3) % VX]));
+        } else {
+          *reinterpret_cast<double2 *>(dst + c) = make_double2(double(v[c]), double(v[(c + 1) % VX]));
+        }
       }
     } else {
 #pragma unroll

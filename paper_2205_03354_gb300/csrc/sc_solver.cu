@@ -22,8 +22,10 @@ namespace sc {
 // kernels
 // ---------------------------------------------------------------------------
 
-template <typename TI, int R>
-__global__ void __launch_bounds__(CG_NTHR, 3)
+// DIMS: 1 = 2D problems only, 2 = 3D only, 3 = both (a kernel holding only
+// the tile routines it needs uses fewer registers, so more CTAs fit).
+template <typename TI, int R, int DIMS>
+__global__ void __launch_bounds__(CG_NTHR, DIMS == 3 ? 3 : 4)
     cg_persistent_kernel(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob,
                          long long budget, unsigned long long slice_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -34,10 +36,12 @@ __global__ void __launch_bounds__(CG_NTHR, 3)
   const SolveProb &P = probs[pi];
   if (P.st->phase == 2) return;
   GroupCtx G{&P, int(blockIdx.x) - P.cta0, 0u, 0u, red, &flag};
-  if (P.ndim == 2)
-    cg_run<TI, 2, R>(G, smem, budget, slice_ns);
-  else
-    cg_run<TI, 3, R>(G, smem, budget, slice_ns);
+  if (DIMS & 1) {
+    if (P.ndim == 2) cg_run<TI, 2, R>(G, smem, budget, slice_ns);
+  }
+  if (DIMS & 2) {
+    if (P.ndim == 3) cg_run<TI, 3, R>(G, smem, budget, slice_ns);
+  }
 }
 
 // out = ring of g (padded array), interior set to zero.
@@ -187,7 +191,7 @@ __global__ void k_ch_stats_part(const double *__restrict__ u, int ndim, int nx, 
 
 template <typename T, int NDIM, int R>
 static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
-  using K = FlatApply<T, NDIM, R, CLS_CROSS2>;
+  using K = FlatApply<T, NDIM, R, CLS_CROSS2, 1>;
   const long long nx = sp.n[0], ny = sp.n[1], nz = NDIM == 3 ? sp.n[2] : 1;
   const long long txy = ((nx + K::BX - 1) / K::BX) * (NDIM == 3 ? (ny + K::BY - 1) / K::BY : 1);
   const long long planes = NDIM == 3 ? nz : ny;
@@ -205,10 +209,10 @@ static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
 
 static size_t smem_bytes_cg() {
   size_t m = 0;
-  m = std::max(m, FlatApply<float, 2, 2, CLS_CROSS2>::SMEM);
-  m = std::max(m, FlatApply<float, 3, 2, CLS_CROSS2>::SMEM);
-  m = std::max(m, FlatApply<double, 2, 2, CLS_CROSS2>::SMEM);
-  m = std::max(m, FlatApply<double, 3, 2, CLS_CROSS2>::SMEM);
+  m = std::max(m, FlatApply<float, 2, 2, CLS_CROSS2, 1>::SMEM);
+  m = std::max(m, FlatApply<float, 3, 2, CLS_CROSS2, 1>::SMEM);
+  m = std::max(m, FlatApply<double, 2, 2, CLS_CROSS2, 1>::SMEM);
+  m = std::max(m, FlatApply<double, 3, 2, CLS_CROSS2, 1>::SMEM);
   return m;
 }
 
@@ -378,14 +382,28 @@ static int assign_groups(std::vector<SolveProb> &hp, const std::vector<int> &idx
   return SC_OK;
 }
 
+typedef void (*CgKernel)(const SolveProb *, const int *, long long, unsigned long long);
+
 template <typename TI>
-static size_t cg_smem_setup() {
-  auto kern = cg_persistent_kernel<TI, 2>;
+static CgKernel cg_kernel_for(int dims) {
+  return dims == 1 ? cg_persistent_kernel<TI, 2, 1> : dims == 2 ? cg_persistent_kernel<TI, 2, 2>
+                                                               : cg_persistent_kernel<TI, 2, 3>;
+}
+
+// Which dimensionalities occur among hp[idx] (bit 0: 2D, bit 1: 3D).
+static int dims_mask(const std::vector<SolveProb> &hp, const std::vector<int> &idx) {
+  int m = 0;
+  for (int i : idx) m |= hp[i].ndim == 2 ? 1 : 2;
+  return m ? m : 1;
+}
+
+template <typename TI>
+static size_t cg_smem_setup(int dims) {
   const size_t smem = smem_bytes_cg();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr = true;
+  static bool attr[4] = {false, false, false, false};
+  if (!attr[dims]) {
+    cudaFuncSetAttribute(cg_kernel_for<TI>(dims), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    attr[dims] = true;
   }
   return smem;
 }
@@ -394,9 +412,9 @@ static size_t cg_smem_setup() {
 // the device (capturable in a CUDA graph).
 template <typename TI>
 static int enqueue_cg(const SolveProb *dprobs, const int *dmap, int grid, cudaStream_t st, long long budget,
-                      unsigned long long slice_ns) {
-  auto kern = cg_persistent_kernel<TI, 2>;
-  const size_t smem = cg_smem_setup<TI>();
+                      unsigned long long slice_ns, int dims) {
+  auto kern = cg_kernel_for<TI>(dims);
+  const size_t smem = cg_smem_setup<TI>(dims);
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(grid);
@@ -419,8 +437,9 @@ template <typename TI>
 static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx, SolveProb *dprobs,
                         int *dmap, unsigned *dbars, cudaStream_t st, long long budget,
                         double slice_ms) {
-  auto kern = cg_persistent_kernel<TI, 2>;
-  const size_t smem = cg_smem_setup<TI>();
+  const int dims = dims_mask(hp, idx);
+  auto kern = cg_kernel_for<TI>(dims);
+  const size_t smem = cg_smem_setup<TI>(dims);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, CG_NTHR, smem);
   if (nb < 1) return fail(SC_ECUDA, "persistent CG kernel does not fit on an SM");
@@ -431,20 +450,20 @@ static int launch_group(std::vector<SolveProb> &hp, const std::vector<int> &idx,
   cudaMemcpyAsync(dmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(dbars, 0, hp.size() * 2 * sizeof(unsigned), st);
   const unsigned long long slice_ns = slice_ms > 0.0 ? (unsigned long long)(slice_ms * 1e6) : 0ull;
-  if (int rc = enqueue_cg<TI>(dprobs, dmap, int(map.size()), st, budget, slice_ns)) return rc;
+  if (int rc = enqueue_cg<TI>(dprobs, dmap, int(map.size()), st, budget, slice_ns, dims)) return rc;
   // pageable sources above: finish before the vectors go out of scope
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(SC_ECUDA, "persistent CG: %s", cudaGetErrorString(e));
   return SC_OK;
 }
 
-int max_group_ctas(bool mixed) {
+int max_group_ctas(bool mixed, int dims) {
   const size_t smem = smem_bytes_cg();
   int nb = 0;
   if (mixed)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_persistent_kernel<float, 2>, CG_NTHR, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_kernel_for<float>(dims), CG_NTHR, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_persistent_kernel<double, 2>, CG_NTHR, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_kernel_for<double>(dims), CG_NTHR, smem);
   return std::max(1, nb) * num_sms();
 }
 
@@ -456,7 +475,7 @@ int run_persistent(std::vector<SolveProb> &hp, SolveProb *dprobs, int *dmap, uns
     std::vector<int> all;
     for (size_t i = 0; i < hp.size(); ++i)
       if (hp[i].mixed == mixed) all.push_back(int(i));
-    const int G = max_group_ctas(mixed);
+    const int G = max_group_ctas(mixed, dims_mask(hp, all));
     for (size_t w0 = 0; w0 < all.size(); w0 += size_t(G)) {
       std::vector<int> idx(all.begin() + w0, all.begin() + std::min(all.size(), w0 + size_t(G)));
       int rc = mixed ? launch_group<float>(hp, idx, dprobs, dmap, dbars, st, budget, slice_ms)
@@ -831,9 +850,10 @@ int sc_ch_run(const sc_ch *c, double *u_dev, int64_t nsteps, int32_t use_graph, 
   for (size_t i = 0; i < sps.size(); ++i)
     if (int rc = upload_prob(sps[i], hp[i], aux[i], st)) return rc;
   const bool mixed = hp[0].mixed != 0;
-  const int G = max_group_ctas(mixed);
   std::vector<int> idx(sps.size()), map;
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = int(i);
+  const int dims = dims_mask(hp, idx);
+  const int G = max_group_ctas(mixed, dims);
   if (int rc = assign_groups(hp, idx, G, dbars, map)) return rc;
   cudaMemcpyAsync(dprobs, hp.data(), hp.size() * sizeof(SolveProb), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -846,8 +866,8 @@ int sc_ch_run(const sc_ch *c, double *u_dev, int64_t nsteps, int32_t use_graph, 
       if (int rc = setup_ch(c, sps[i], hp[i], aux[i], st)) return rc;
     k_reset_states<<<(n + 127) / 128, 128, 0, st>>>(dprobs, n);
     cudaMemsetAsync(dbars, 0, size_t(n) * 2 * sizeof(unsigned), st);
-    int rc = mixed ? enqueue_cg<float>(dprobs, dmap, int(map.size()), st, LLONG_MAX, 0ull)
-                   : enqueue_cg<double>(dprobs, dmap, int(map.size()), st, LLONG_MAX, 0ull);
+    int rc = mixed ? enqueue_cg<float>(dprobs, dmap, int(map.size()), st, LLONG_MAX, 0ull, dims)
+                   : enqueue_cg<double>(dprobs, dmap, int(map.size()), st, LLONG_MAX, 0ull, dims);
     if (rc) return rc;
     k_record_states<<<1, 128, 0, st>>>(dprobs, n, dinfo, dstep);
     return SC_OK;

@@ -265,12 +265,20 @@ __device__ __forceinline__ void tile_origin(const SolveProb &P, int tile, int H,
   }
 }
 
+// The problem's weight boxes, staged in shared memory once per launch.
+struct CgWeights {
+  double w64[125];
+  float w32[125];
+};
+
 // Phase A: q = A p over the group's tiles.
 template <typename T, int NDIM, int R>
-__device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, double *red) {
-  using K = FlatApply<T, NDIM, R, CLS_CROSS2>;
+__device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, double *red,
+                            const CgWeights &cw) {
+  using K = FlatApply<T, NDIM, R, CLS_CROSS2, 1>;
   const ApplyGeom g = cg_geom<T, NDIM, R>(P, P.H_in);
-  const WBox<T, NDIM, R> W = *reinterpret_cast<const WBox<T, NDIM, R> *>(P.wT);
+  const WBox<T, NDIM, R> &W = *reinterpret_cast<const WBox<T, NDIM, R> *>(
+      sizeof(T) == 8 ? static_cast<const void *>(cw.w64) : static_cast<const void *>(cw.w32));
   for (int tile = rank; tile < P.ntiles_in; tile += P.ncta) {
     int x0, y0, z0;
     tile_origin<K>(P, tile, P.H_in, NDIM, x0, y0, z0);
@@ -285,10 +293,11 @@ __device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, d
 // FP64 residual r = rhs - A x over the FP64 tiles; partial r.r in slot 0 and
 // (when mean_fix) partial sum(x) in slot 1.
 template <int NDIM, int R>
-__device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, double *red) {
-  using K = FlatApply<double, NDIM, R, CLS_CROSS2>;
+__device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, double *red,
+                            const CgWeights &cw) {
+  using K = FlatApply<double, NDIM, R, CLS_CROSS2, 1>;
   const ApplyGeom g = cg_geom<double, NDIM, R>(P, P.H_64);
-  const WBox<double, NDIM, R> W = *reinterpret_cast<const WBox<double, NDIM, R> *>(P.w64);
+  const WBox<double, NDIM, R> &W = *reinterpret_cast<const WBox<double, NDIM, R> *>(cw.w64);
   for (int tile = rank; tile < P.ntiles_64; tile += P.ncta) {
     int x0, y0, z0;
     tile_origin<K>(P, tile, P.H_64, NDIM, x0, y0, z0);
@@ -483,6 +492,15 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
                        unsigned long long slice_ns) {
   const SolveProb &P = *G.P;
   const unsigned long long deadline = slice_ns ? global_ns() + slice_ns : 0ull;
+  __shared__ CgWeights cw;
+  {
+    constexpr int NB = NDIM == 3 ? 125 : 25;
+    for (int i = threadIdx.x; i < NB; i += CG_NTHR) {
+      cw.w64[i] = P.w64[i];
+      cw.w32[i] = P.mixed ? static_cast<const float *>(P.wT)[i] : 0.0f;
+    }
+    __syncthreads();
+  }
   SolveState &S = *P.st;
   double red_out[4];
   double *red = G.red;
@@ -495,7 +513,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
 
   if (phase == 0) {
     // r = rhs - A x0 (FP64); rh = r; p = rh
-    phase_resid<NDIM, R>(P, G.rank, smem, red);
+    phase_resid<NDIM, R>(P, G.rank, smem, red, cw);
     if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
     phase_vec<TI, 0>(P, G.rank, 0.0, red);
     if (!group_reduce(G, 3, P.nchunks, red_out)) return;
@@ -517,7 +535,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
       break;
     }
     // A: q = A p, p.q
-    phase_apply<TI, NDIM, R>(P, G.rank, smem, red);
+    phase_apply<TI, NDIM, R>(P, G.rank, smem, red, cw);
     if (!group_reduce(G, 1, P.ntiles_in, red_out)) return;
     const double pq = red_out[0];
     if (!finite_pos(pq) || !(rr == rr)) {
@@ -547,7 +565,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
         phase_vec<TI, 3>(P, G.rank, 0.0, red);
         if (!group_reduce(G, 0, 0, red_out)) return;
       }
-      phase_resid<NDIM, R>(P, G.rank, smem, red);
+      phase_resid<NDIM, R>(P, G.rank, smem, red, cw);
       if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
       ++outer;
       rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
@@ -585,7 +603,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
       phase_vec<TI, 6>(P, G.rank, c, red);
       if (!group_reduce(G, 0, 0, red_out)) return;
     }
-    phase_resid<NDIM, R>(P, G.rank, smem, red);
+    phase_resid<NDIM, R>(P, G.rank, smem, red, cw);
     if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
     rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
     if (status == SC_OK && !(rel <= tol)) {

@@ -45,7 +45,8 @@ struct Carver {
 };
 
 double kappa_estimate(const ProbSpec &sp, double h);
-int max_group_ctas(bool mixed);
+// Resident persistent-CG CTAs on the device (dims: bit 0 2D, bit 1 3D).
+int max_group_ctas(bool mixed, int dims = 3);
 int bvp_spec(const sc_bvp *b, ProbSpec &sp);
 // Work-space layout of one problem (sizes only when cv.base == nullptr).
 void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux);
