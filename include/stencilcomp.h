@@ -345,6 +345,14 @@ int sc_ch_stats_noalloc(const sc_ch *p, const double *u_dev, double *mass_host, 
                         sc_stream_t stream);
 
 
+/* Failure-detection self-test of the solver's bounded group barrier: runs
+ * the barrier for a group of two CTAs with only one launched, so the release
+ * never comes; the wait gives up after spin_limit polls (1..2^24, ~100 ns
+ * each) and *status_out receives SC_ETIMEOUT.  Nothing traps or faults; the
+ * context stays usable.  work_bytes >= 4096. */
+int sc_selftest_barrier_timeout(void *work_dev, size_t work_bytes, int64_t spin_limit, int32_t *status_out,
+                                sc_stream_t stream);
+
 /* ---- Serving loop: continuous batching of plate-problem solves ------------- */
 
 /* A server owns one scheduler thread on the device that is current when it is

@@ -102,7 +102,9 @@ struct FlatApply {
   static constexpr int PXS = BX + 2 * HX;       // smem row length
   static constexpr int PYS = BY + 2 * RP;       // smem rows per plane
   static constexpr int PLANE = PXS * PYS;
-  static constexpr int NSTAGE = 3;
+  // planes in the ring: streaming applies (family 0) keep 2 in flight; the
+  // solver's short tiles (family 1) are L2-latency bound and keep more
+  static constexpr int NSTAGE = FAM == 0 ? 3 : (NDIM == 2 ? 8 : 4);
   static constexpr int NS = 2 * R + 1;          // pending output planes
   static constexpr int NCHUNK = PLANE / CH;
   static constexpr int CPT = (NCHUNK + NTHR - 1) / NTHR;  // chunks per thread

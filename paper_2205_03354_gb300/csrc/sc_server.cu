@@ -20,6 +20,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "sc_apply_host.h"
 #include "sc_internal.h"
 #include "sc_solver.cuh"
 #include "sc_solver_host.h"
@@ -145,6 +146,7 @@ struct sc_server {
   sc::SolveProb *dprobs = nullptr;
   int *dmap = nullptr;
   unsigned *dbars = nullptr;
+  sc::SolveState *dstates = nullptr;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<sc::Req *> pending;
@@ -233,8 +235,7 @@ static void worker_loop(sc_server *S) {
     for (size_t i = 0; i < act.size(); ++i) hp[i] = act[i]->P;
     int rc = run_persistent(hp, S->dprobs, S->dmap, S->dbars, S->st, LLONG_MAX, S->cfg.slice_ms);
     std::vector<SolveState> hs(act.size());
-    for (size_t i = 0; i < act.size(); ++i)
-      cudaMemcpyAsync(&hs[i], act[i]->P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, S->st);
+    if (!rc) rc = gather_states(S->dprobs, int(act.size()), S->dstates, hs.data(), S->st);
     cudaError_t e = cudaStreamSynchronize(S->st);
     if (rc || e != cudaSuccess) {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -284,11 +285,14 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
   if (!cfg || !out || !cfg->arena_dev) return fail(SC_EINVAL, "null argument");
   if (cfg->max_active < 1 || cfg->max_active > 4096) return fail(SC_EINVAL, "max_active must be 1..4096");
   if (!(cfg->slice_ms > 0.0)) return fail(SC_EINVAL, "slice_ms must be positive");
-  const int G = std::max(max_group_ctas(true), max_group_ctas(false));
+  // the CTA -> problem map must hold the largest grid any persistent-kernel
+  // variant can launch: bound it by the hardware limit of resident CTAs
+  const int G = 32 * num_sms();
   Carver head(nullptr, 0);
   head.take(size_t(cfg->max_active) * sizeof(SolveProb));
   head.take(size_t(G) * sizeof(int));
   head.take(size_t(cfg->max_active) * 2 * sizeof(unsigned));
+  head.take(size_t(cfg->max_active) * sizeof(SolveState));
   const size_t hbytes = (head.off + 255) & ~size_t(255);
   if (cfg->arena_bytes <= hbytes + 4096) return fail(SC_ENOMEM, "arena smaller than the server's descriptors");
   sc_server *S = new sc_server();
@@ -302,6 +306,7 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
   S->dprobs = static_cast<SolveProb *>(hc.take(size_t(cfg->max_active) * sizeof(SolveProb)));
   S->dmap = static_cast<int *>(hc.take(size_t(G) * sizeof(int)));
   S->dbars = static_cast<unsigned *>(hc.take(size_t(cfg->max_active) * 2 * sizeof(unsigned)));
+  S->dstates = static_cast<SolveState *>(hc.take(size_t(cfg->max_active) * sizeof(SolveState)));
   S->arena_base = static_cast<char *>(cfg->arena_dev) + hbytes;
   S->arena_size = cfg->arena_bytes - hbytes;
   S->arena.reset(S->arena_size);

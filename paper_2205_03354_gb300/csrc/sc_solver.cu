@@ -24,6 +24,7 @@ namespace sc {
 
 // DIMS: 1 = 2D problems only, 2 = 3D only, 3 = both (a kernel holding only
 // the tile routines it needs uses fewer registers, so more CTAs fit).
+// TI = void: both precision classes in one launch, chosen per problem.
 template <typename TI, int R, int DIMS>
 __global__ void __launch_bounds__(CG_NTHR, DIMS == 3 ? 3 : 4)
     cg_persistent_kernel(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob,
@@ -41,6 +42,27 @@ __global__ void __launch_bounds__(CG_NTHR, DIMS == 3 ? 3 : 4)
   }
   if (DIMS & 2) {
     if (P.ndim == 3) cg_run<TI, 3, R>(G, smem, budget, slice_ns);
+  }
+}
+
+template <int R, int DIMS>
+__global__ void __launch_bounds__(CG_NTHR, 3)
+    cg_persistent_both(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob, long long budget,
+                       unsigned long long slice_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[CG_NTHR / 32];
+  __shared__ int flag;
+  const int pi = cta_prob[blockIdx.x];
+  if (pi < 0) return;
+  const SolveProb &P = probs[pi];
+  if (P.st->phase == 2) return;
+  GroupCtx G{&P, int(blockIdx.x) - P.cta0, 0u, 0u, red, &flag};
+  if (P.mixed) {
+    if ((DIMS & 1) && P.ndim == 2) cg_run<float, 2, R>(G, smem, budget, slice_ns);
+    if ((DIMS & 2) && P.ndim == 3) cg_run<float, 3, R>(G, smem, budget, slice_ns);
+  } else {
+    if ((DIMS & 1) && P.ndim == 2) cg_run<double, 2, R>(G, smem, budget, slice_ns);
+    if ((DIMS & 2) && P.ndim == 3) cg_run<double, 3, R>(G, smem, budget, slice_ns);
   }
 }
 
@@ -368,7 +390,7 @@ static int assign_groups(std::vector<SolveProb> &hp, const std::vector<int> &idx
     nc[k] = c;
     used += c;
   }
-  if (used > G) return fail(SC_EINVAL, "internal: CTA assignment exceeds the grid");
+  if (used > G || G > 32 * num_sms()) return fail(SC_EINVAL, "internal: CTA assignment exceeds the grid");
   map.assign(used, -1);
   int c0 = 0;
   for (size_t k = 0; k < idx.size(); ++k) {
@@ -388,6 +410,10 @@ template <typename TI>
 static CgKernel cg_kernel_for(int dims) {
   return dims == 1 ? cg_persistent_kernel<TI, 2, 1> : dims == 2 ? cg_persistent_kernel<TI, 2, 2>
                                                                : cg_persistent_kernel<TI, 2, 3>;
+}
+template <>
+CgKernel cg_kernel_for<void>(int dims) {
+  return dims == 1 ? cg_persistent_both<2, 1> : dims == 2 ? cg_persistent_both<2, 2> : cg_persistent_both<2, 3>;
 }
 
 // Which dimensionalities occur among hp[idx] (bit 0: 2D, bit 1: 3D).
@@ -471,10 +497,27 @@ int max_group_ctas(bool mixed, int dims) {
 // beyond the grid size).
 int run_persistent(std::vector<SolveProb> &hp, SolveProb *dprobs, int *dmap, unsigned *dbars,
                    cudaStream_t st, long long budget, double slice_ms) {
+  bool has[2] = {false, false};
+  for (const SolveProb &P : hp) has[P.mixed ? 1 : 0] = true;
+  if (has[0] && has[1]) {
+    // both precision classes share one launch (each problem picks its path)
+    std::vector<int> all(hp.size());
+    for (size_t i = 0; i < hp.size(); ++i) all[i] = int(i);
+    const int dims = dims_mask(hp, all);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_kernel_for<void>(dims), CG_NTHR, smem_bytes_cg());
+    const int G = std::max(1, nb) * num_sms();
+    for (size_t w0 = 0; w0 < all.size(); w0 += size_t(G)) {
+      std::vector<int> idx(all.begin() + w0, all.begin() + std::min(all.size(), w0 + size_t(G)));
+      if (int rc = launch_group<void>(hp, idx, dprobs, dmap, dbars, st, budget, slice_ms)) return rc;
+    }
+    return SC_OK;
+  }
   for (int mixed = 0; mixed < 2; ++mixed) {
     std::vector<int> all;
     for (size_t i = 0; i < hp.size(); ++i)
       if (hp[i].mixed == mixed) all.push_back(int(i));
+    if (all.empty()) continue;
     const int G = max_group_ctas(mixed, dims_mask(hp, all));
     for (size_t w0 = 0; w0 < all.size(); w0 += size_t(G)) {
       std::vector<int> idx(all.begin() + w0, all.begin() + std::min(all.size(), w0 + size_t(G)));
@@ -684,7 +727,7 @@ size_t batch_bytes(const std::vector<ProbSpec> &sps) {
     cv.take(std::max<long long>(P.npts, 1) * 8);  // ones vector (plain mean fix)
   }
   cv.take(sps.size() * sizeof(SolveProb));
-  cv.take(sizeof(int) * size_t(8) * 1024 * 16);  // CTA map (max grid)
+  cv.take(sizeof(int) * size_t(32) * num_sms());  // CTA map (max grid)
   cv.take(sps.size() * 2 * sizeof(unsigned));
   return cv.off + 256;
 }
@@ -712,7 +755,7 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
     aux[i].ones = static_cast<double *>(cv.take(std::max<long long>(hp[i].npts, 1) * 8));
   }
   SolveProb *dprobs = static_cast<SolveProb *>(cv.take(sps.size() * sizeof(SolveProb)));
-  int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(8) * 1024 * 16));
+  int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(32) * num_sms()));
   unsigned *dbars = static_cast<unsigned *>(cv.take(sps.size() * 2 * sizeof(unsigned)));
   for (size_t i = 0; i < sps.size(); ++i) {
     if (int rc = upload_prob(sps[i], hp[i], aux[i], st)) return rc;
@@ -766,6 +809,20 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
   return SC_OK;
 }
 
+// out[i] = *probs[i].st for i < n (one contiguous read-back).
+__global__ void k_gather_states(const SolveProb *__restrict__ probs, int n, SolveState *__restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = *probs[i].st;
+}
+
+int gather_states(const SolveProb *dprobs, int n, SolveState *dout, SolveState *host, cudaStream_t st) {
+  if (n <= 0) return SC_OK;
+  k_gather_states<<<(n + 127) / 128, 128, 0, st>>>(dprobs, n, dout);
+  cudaMemcpyAsync(host, dout, size_t(n) * sizeof(SolveState), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "state read-back: %s", cudaGetErrorString(e));
+  return SC_OK;
+}
+
 // Resets every problem's solver state (a graph node in the multi-step run).
 __global__ void k_reset_states(const SolveProb *__restrict__ probs, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -794,11 +851,50 @@ __global__ void k_record_states(const SolveProb *__restrict__ probs, int n, Solv
   if (i == 0) *step = k + 1;
 }
 
+// A group of two CTAs of which only one is launched: its barrier can never
+// be released, so the bounded wait must run out and report SC_ETIMEOUT.
+__global__ void k_barrier_timeout_probe(SolveProb *P, long long spin_limit) {
+  __shared__ double red[CG_NTHR / 32];
+  __shared__ int flag;
+  GroupCtx G{P, 0, 0u, 0u, red, &flag, spin_limit};
+  double out[4];
+  if (threadIdx.x == 0) P->part[0] = 1.0;
+  group_reduce(G, 1, 1, out);
+}
+
 }  // namespace sc
 
 using namespace sc;
 
 extern "C" {
+
+int sc_selftest_barrier_timeout(void *work_dev, size_t work_bytes, int64_t spin_limit, int32_t *status_out,
+                                sc_stream_t stream) {
+  if (!work_dev || !status_out || spin_limit < 1 || spin_limit > (1LL << 24))
+    return fail(SC_EINVAL, "bad argument");
+  if (work_bytes < 4096) return fail(SC_ENOMEM, "work space too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  char *w = static_cast<char *>(work_dev);
+  SolveProb P;
+  std::memset(&P, 0, sizeof(P));
+  P.ncta = 2;  // a second member that never arrives
+  P.nslot = 8;
+  P.part = reinterpret_cast<double *>(w + 1024);
+  P.scal = reinterpret_cast<double *>(w + 1536);
+  P.bar = reinterpret_cast<unsigned *>(w + 1792);
+  P.st = reinterpret_cast<SolveState *>(w + 2048);
+  SolveProb *dP = reinterpret_cast<SolveProb *>(w);
+  cudaMemsetAsync(w + 1024, 0, 2048, st);
+  cudaMemcpyAsync(dP, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+  k_barrier_timeout_probe<<<1, CG_NTHR, 0, st>>>(dP, spin_limit);
+  SolveState s;
+  cudaMemcpyAsync(&s, P.st, sizeof(s), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "self-test: %s", cudaGetErrorString(e));
+  *status_out = s.status;
+  clear_error();
+  return SC_OK;
+}
 
 size_t sc_ch_run_work_bytes(const sc_ch *c, int64_t nsteps) {
   if (ch_validate(c) || nsteps < 1) return 0;
@@ -843,7 +939,7 @@ int sc_ch_run(const sc_ch *c, double *u_dev, int64_t nsteps, int32_t use_graph, 
     aux[i].ones = static_cast<double *>(cv.take(std::max<long long>(hp[i].npts, 1) * 8));
   }
   SolveProb *dprobs = static_cast<SolveProb *>(cv.take(sps.size() * sizeof(SolveProb)));
-  int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(8) * 1024 * 16));
+  int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(32) * num_sms()));
   unsigned *dbars = static_cast<unsigned *>(cv.take(sps.size() * 2 * sizeof(unsigned)));
   SolveState *dinfo = static_cast<SolveState *>(cv.take(size_t(nsteps) * sps.size() * sizeof(SolveState)));
   int *dstep = static_cast<int *>(cv.take(sizeof(int)));

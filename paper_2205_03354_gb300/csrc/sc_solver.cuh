@@ -90,6 +90,7 @@ struct GroupCtx {
   unsigned gen;     // release generation
   double *red;      // shared scratch (>= CG_NTHR/32 doubles)
   int *flag;        // shared int
+  long long spin_limit = SPIN_LIMIT;
 };
 
 __device__ __forceinline__ double fixed_sum(const double *a, int n, double *red) {
@@ -154,7 +155,7 @@ __device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *ou
     } else if (threadIdx.x == 0) {
       long long spins = 0;
       while (ld_acquire(&P.bar[1]) < G.gen) {
-        if (++spins > SPIN_LIMIT) {
+        if (++spins > G.spin_limit) {
           *G.flag = -1;
           break;
         }

@@ -54,6 +54,10 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux);
 int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
 // Right-hand side b = g - A(ring) and x = 0 of a plate problem (enqueued).
 int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
+struct SolveState;
+// Copies the solver states of the n problems described at dprobs to host
+// (one gather kernel into dout, one copy; synchronous).
+int gather_states(const SolveProb *dprobs, int n, SolveState *dout, SolveState *host, cudaStream_t st);
 // Runs the persistent engine over `hp` (both precision classes) for at most
 // `budget` iterations or `slice_ms` milliseconds per launch (0: no limit);
 // synchronous.  dprobs/dmap/dbars: device descriptor space.

@@ -199,3 +199,18 @@ def ch_run(c: Ch, u: torch.Tensor, nsteps: int, use_graph=True, work=None, strea
                         ctypes.c_void_p(w.data_ptr()), nb, infos, stream_arg(stream)))
     d = [i.as_dict() for i in infos]
     return [d[k * c.batch:(k + 1) * c.batch] for k in range(nsteps)]
+
+
+lib.sc_selftest_barrier_timeout.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]
+lib.sc_selftest_barrier_timeout.restype = ctypes.c_int
+
+
+def selftest_barrier_timeout(spin_limit: int = 1 << 14, stream=None) -> int:
+    """Runs the solver barrier with a member that never arrives; returns the
+    status the bounded wait reports (SC_ETIMEOUT = 5)."""
+    w = torch.empty(4096, dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+    st = ctypes.c_int32(-1)
+    check(lib.sc_selftest_barrier_timeout(ctypes.c_void_p(w.data_ptr()), 4096, spin_limit, ctypes.byref(st),
+                                          stream_arg(stream)))
+    return st.value

@@ -94,3 +94,29 @@ def test_small_arena_queues_and_admits_as_memory_frees():
         assert e.value.status == 2  # SC_ENOMEM
     finally:
         srv.close()
+
+
+def test_burst_of_many_requests_all_converge():
+    """Many small requests of both dimensions at once: the persistent launch
+    then spans most of the GPU (the CTA map is at its largest); every result
+    must converge and match its solo solve."""
+    arena = torch.empty(2 << 30, dtype=torch.uint8, device=DEV)
+    srv = sc.Server(arena, max_active=512, slice_ms=1.0)
+    rng = np.random.default_rng(9)
+    try:
+        jobs = []
+        for k in range(160):
+            nd = 2 if k % 3 else 3
+            n = int(rng.integers(12, 48)) if nd == 2 else int(rng.integers(8, 16))
+            f, g = _case(n, nd, tuple(int(v) for v in rng.integers(1, 4, size=nd)))
+            x = np.full(f.shape, np.nan)
+            jobs.append((srv.submit(f, g, x, prec="auto"), f, g, x))
+        srv.drain(600.0)
+        for t, f, g, x in jobs:
+            r = srv.poll(t)
+            assert r["status"] == 0 and r["rel_res"] <= 1e-10, r
+        for t, f, g, x in jobs[:12]:
+            solo, info = _solo(f, g, "auto")
+            assert np.array_equal(solo, x)
+    finally:
+        srv.close()

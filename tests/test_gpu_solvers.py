@@ -196,3 +196,14 @@ def test_ch_run_graph_equals_steps(ndim, n, batch, prec):
     # mass conserved over the run
     for b in range(batch):
         assert abs(float(ua[b].sum()) - u0[b].sum()) <= 1e-12 * np.abs(u0[b]).sum()
+
+
+def test_bounded_barrier_wait_reports_timeout():
+    """Failure detection without a GPU fault: a group barrier whose second
+    member never arrives gives up after its spin limit and reports
+    SC_ETIMEOUT; the context keeps working afterwards."""
+    from paper_2205_03354_gb300.solvers import selftest_barrier_timeout
+    assert selftest_barrier_timeout(1 << 12) == 5
+    m, f, g, x = bvp_inputs(16, 2)
+    info = sc.solve_biharmonic(f, g, x, prec="f64", rtol=RTOL)
+    assert info["status"] == 0 and info["rel_res"] <= RTOL
