@@ -216,6 +216,14 @@ int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dty
 /* The cached choice for a shape (SC_EINVAL if not tuned). */
 int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
                     const int64_t *dims, sc_tune_choice *out);
+/* Records a choice for a shape in the process cache without timing, e.g. one
+ * saved from an earlier sc_autotune_apply run, so that sc_apply_tuned reuses
+ * it (a later sc_autotune_apply for the shape replaces it).  eval is an
+ * sc_eval; planes in [0, 4096]; SC_EVAL_PAIR on an operator the pair path
+ * does not cover runs nested native arithmetic.  in->ms is stored as given.
+ * SC_EINVAL for a bad operator, shape or choice; no device work. */
+int sc_tune_set(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                const int64_t *dims, const sc_tune_choice *in);
 
 /* ---- Solvers (device) ------------------------------------------------------ */
 

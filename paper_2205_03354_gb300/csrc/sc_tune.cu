@@ -172,4 +172,21 @@ int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dt
   return SC_OK;
 }
 
+int sc_tune_set(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                const int64_t *dims, const sc_tune_choice *in) {
+  if (!outer || !inner || !dims || !in) return fail(SC_EINVAL, "null argument");
+  if (int rc = validate_apply(outer, dtype, bc, dims, 1, 1)) return rc;
+  if (int rc = validate_apply(inner, dtype, bc, dims, 1, 1)) return rc;
+  if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
+  if (in->eval < SC_EVAL_FLAT || in->eval > SC_EVAL_PAIR) return fail(SC_EINVAL, "unknown eval %d", in->eval);
+  if (in->planes < 0 || in->planes > 4096) return fail(SC_EINVAL, "planes %d out of range", in->planes);
+  sc_stencil C;
+  if (int rc = sc_compose_stencil(outer, inner, &C)) return rc;
+  if (C.radius > SC_MAX_APPLY_RADIUS) return fail(SC_EINVAL, "composed radius too large");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key_of(outer, inner, dtype, bc, dims)] = *in;
+  clear_error();
+  return SC_OK;
+}
+
 }  // extern "C"

@@ -132,6 +132,8 @@ lib.sc_apply_tuned.argtypes = _TUNE_ARGS + [ctypes.c_void_p]
 lib.sc_apply_tuned.restype = ctypes.c_int
 lib.sc_tuned_choice.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.POINTER(TuneChoice)]
 lib.sc_tuned_choice.restype = ctypes.c_int
+lib.sc_tune_set.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.POINTER(TuneChoice)]
+lib.sc_tune_set.restype = ctypes.c_int
 
 
 def _tune_args(outer, inner, x, y, work, bc, h, dims):
@@ -156,3 +158,12 @@ def apply_tuned(outer: Stencil, inner: Stencil, x, y, work, bc="periodic", h=(1,
     """y = compose(outer, inner) x with the tuned schedule for this shape."""
     check(lib.sc_apply_tuned(*_tune_args(outer, inner, x, y, work, bc, h, dims), stream_arg(stream)))
     return y
+
+
+def tune_set(outer: Stencil, inner: Stencil, dtype, bc, dims, choice: dict) -> None:
+    """Records a saved tuning choice ({"eval", "planes", "ms"}) for a shape so
+    that apply_tuned reuses it without timing."""
+    names = {v: k for k, v in EVAL_NAMES.items()}
+    c = TuneChoice(names[choice["eval"]], int(choice["planes"]), float(choice.get("ms", 0.0)))
+    check(lib.sc_tune_set(ctypes.byref(outer), ctypes.byref(inner), dtype_code(dtype), bc_code(bc),
+                          dims_arg(dims), ctypes.byref(c)))

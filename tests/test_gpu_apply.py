@@ -305,3 +305,23 @@ def test_autotuned_apply_matches_oracle(ndim, n, dt):
         mag = oap.apply(ost.fp_weights(ost.compose(absL, absL), Fraction(1, n), np.float64),
                         np.abs(x.astype(np.float64)), "periodic", oc.radius)
         assert np.all(np.abs(yt.cpu().numpy() - y_ref) <= tol * mag)
+
+
+@pytest.mark.parametrize("how,planes", [("flat", 16), ("nested", 0), ("pair", 32)])
+def test_saved_tuning_runs_the_recorded_schedule(how, planes):
+    """A choice recorded with tune_set is what apply_tuned runs: the same bits
+    as calling that schedule directly."""
+    n = 48
+    L = sc.laplacian(3, 4)
+    x = torch.from_numpy(fields.uniform((n,) * 3, seed=77, dtype=np.float64)).to(DEV)
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    wb = sc.apply_composition_work_bytes(L, L, x.dtype, "periodic", (n,) * 3)
+    work = torch.empty(wb, dtype=torch.uint8, device=DEV)
+    sc.tune_set(L, L, x.dtype, "periodic", (n,) * 3, {"eval": how, "planes": planes, "ms": 0.0})
+    sc.apply_tuned(L, L, x, y1, work, h=(1, n))
+    if how == "flat":
+        sc.apply_composed(sc.compose_stencil(L, L), x, y2, h=(1, n))
+    else:
+        sc.apply_composition(L, L, x, y2, work, h=(1, n), arith="pair" if how == "pair" else "native")
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)

@@ -87,3 +87,22 @@ def test_errors_are_reported():
         sc.laplacian(4, 2)
     with pytest.raises(sc.ScError):
         sc.stencil_weights(a, 0, 1)
+
+
+def test_saved_tuning_round_trips_without_a_gpu():
+    """A saved tuning choice is recorded and read back by the host cache; bad
+    choices are rejected before any device work."""
+    import torch
+    from paper_2205_03354_gb300.ops import TuneChoice, dims_arg, lib
+    L = sc.laplacian(3, 2)
+    sc.tune_set(L, L, torch.float64, "periodic", (40, 36, 20), {"eval": "pair", "planes": 32, "ms": 1.5})
+    out = TuneChoice()
+    assert lib.sc_tuned_choice(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
+                               dims_arg((40, 36, 20)), ctypes.byref(out)) == 0
+    assert out.as_dict() == {"eval": "pair", "planes": 32, "ms": 1.5}
+    # another shape stays untuned
+    assert lib.sc_tuned_choice(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
+                               dims_arg((40, 36, 21)), ctypes.byref(out)) == 1
+    for bad in (TuneChoice(3, 0, 0.0), TuneChoice(0, -1, 0.0), TuneChoice(1, 5000, 0.0)):
+        assert lib.sc_tune_set(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
+                               dims_arg((40, 36, 20)), ctypes.byref(bad)) == 1
