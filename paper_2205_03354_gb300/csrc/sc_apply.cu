@@ -251,10 +251,8 @@ int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int
   int *flag = reinterpret_cast<int *>(w + tb + xpb);
   // pair arithmetic for FP64 Laplacian compositions (see sc_apply_df.cu)
   float ca[3], cb[3];
-  const bool pair = arith == SC_ARITH_PAIR && dtype == SC_F64 && rA == rB && star_int_form(A, ca, ca + 1, ca + 2) &&
-                    star_int_form(B, cb, cb + 1, cb + 2) && A->hpow == B->hpow && dims[0] % 2 == 0 &&
-                    (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
-                    (bc == SC_BC_PERIODIC || rA == 2);
+  bool pair = arith == SC_ARITH_PAIR && dtype == SC_F64 && rA == rB && star_int_form(A, ca, ca + 1, ca + 2) &&
+              star_int_form(B, cb, cb + 1, cb + 2) && A->hpow == B->hpow;
   double scale = 1.0;
   if (pair) {
     // exact rational 1 / (den_A den_B h^(pA + pB)), rounded once
@@ -269,8 +267,10 @@ int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int
     if (int rc = weights_f64(&one, h_num, h_den, &unit)) return rc;
     scale = unit / (double(A->den) * double(B->den));  // den products are small integers: exact
     if (!(double(A->den) * double(B->den) < 9007199254740992.0)) return fail(SC_EOVERFLOW, "denominator");
-    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    const void *xin = bc == SC_BC_ZERO ? static_cast<const void *>(w + tb) : x;
+    pair = df_supported(nd, rA, dims, bc == SC_BC_PERIODIC ? SC_BC_PERIODIC : SC_BC_GHOSTED, scale, xin, t, y);
   }
+  if (pair) cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (bc == SC_BC_PERIODIC) {
     if (pair) {
       if (int rc = df_composition_enqueue(nd, rA, x, t, y, dims, dims, SC_BC_PERIODIC, ca, cb, scale, flag, st,

@@ -1,18 +1,20 @@
-// FP64 Laplacian passes in double-float arithmetic (pairs of FP32 numbers).
+// FP64 Laplacian passes in double-float arithmetic (pairs of FP32 numbers),
+// two grid points per packed f32x2 instruction.
 //
 // GB300 issues two FP64 FMAs per clock per SM against 128 FP32 FMAs, so an
 // FP64 stencil apply is bound by the FP64 pipe at a few percent of HBM
 // bandwidth.  For the factors of the composed operators used here -- a
 // Laplacian L = s * L_int, L_int with small integer weights c0 (centre),
 // c1 (distance 1) and c2 (distance 2, fourth order) on every axis, s =
-// 1/(den h^2) -- the nested form y = s^2 L_int(L_int x) (Eq. C=B(A)) can be
+// 1/(den h^2) -- the nested form y = s^2 L_int(L_int x) (Eq. C=B(A)) is
 // evaluated on the FP32 pipe instead:
 //   * a double x is split exactly into hi + lo + rest with integer bit
 //     operations (hi: the leading 24 significand bits, lo: the next 29 bits
 //     rounded to 24; |rest| <= 2^-48 |x|);
 //   * sums are carried as unevaluated pairs (hi, lo) with error-free
 //     transformations (Knuth's TwoSum, Dekker's Fast2Sum, TwoProduct via
-//     FMA); products by the integer weights are exact up to the pair format;
+//     FMA) in Neumaier's running-compensation order; products by the integer
+//     weights are exact up to the pair format;
 //   * the scaled result s^2 z is rebuilt as a double exactly from its pair
 //     with integer bit operations and one FP64 addition.
 // Relative error per pass is a few units of 2^-48 of sum_k |w_k x_k|, inside
@@ -21,10 +23,24 @@
 // into normal floats: such a value raises a flag in device memory, and the
 // native FP64 passes that follow the emulated ones (launched unconditionally,
 // each CTA returning at once while the flag is clear) recompute the result.
+//
+// Packing.  sm_103a executes add/sub/mul/fma.rn.f32x2 on register pairs with
+// the rounding of the scalar instructions, one issue slot for two lanes.  The
+// x axis of a row of length n (even) is folded in half: cell c in [0, n/2)
+// holds the points c (lane a) and c + n/2 (lane b).  Every x offset of a
+// stencil then maps a cell to a cell with both lanes in step, so one thread
+// evaluates two points with one instruction stream.  The intermediate of the
+// two passes is kept in this folded layout in HBM, one 16-byte cell
+// {hi_a, hi_b, lo_a, lo_b} per pair of points, so the second pass copies it
+// with 16-byte cp.async and no rearrangement.  Halo cells left of cell 0 and
+// right of cell n/2 - 1 are the cells n/2 away with their lanes swapped
+// (periodic rows; for the ghosted intermediate the lane that is swapped in
+// feeds only points outside the output).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 
@@ -35,249 +51,368 @@
 
 namespace sc {
 
-struct F2 {
-  float h, l;
-};
+typedef unsigned long long f2x;  // two FP32 values, lane a in the low half
 
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
-  F2 r;
-  r.h = a + b;
-  r.l = b - (r.h - a);
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x pk2(float a, float b) {
+  f2x d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ void upk2(f2x d, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(d));
+}
+
+// Two double-float numbers (lanes a and b): value = h + l per lane.
+struct P2 {
+  f2x h, l;
+};
+// Neumaier accumulation: s the running sum, c the collected rounding errors
+// and low parts (unnormalised).
+struct Acc2 {
+  f2x s, c;
+};
+__device__ __forceinline__ void acc_add2(Acc2 &A, f2x vh, f2x vl) {
+  const f2x s = add2(A.s, vh);  // TwoSum(A.s, vh) = (s, e)
+  const f2x bb = sub2(s, A.s);
+  const f2x e = add2(sub2(A.s, sub2(s, bb)), sub2(vh, bb));
+  A.s = s;
+  A.c = add2(A.c, add2(e, vl));
+}
+// Rounded packed products are formed as fma(a, b, Z), Z a zero pair that the
+// kernel receives as an argument.  Measured on sm_103a: products taken with
+// mul.rn.f32x2 and then consumed by the error-free transformations below did
+// not reproduce the scalar mul.rn.f32 results once ptxas optimisation was on
+// (bit-exact at -O0 and with scalar products), so the kernels take no packed
+// mul and the product's rounding is fixed by the FMA.
+__device__ __forceinline__ f2x rmul2(f2x a, f2x b, f2x Z) { return fma2(a, b, Z); }
+
+// A *= k for an integer k exact in FP32 (kk = (k, k), nk = (-k, -k)):
+// TwoProduct of the leading sum, the compensation scaled with one rounding.
+__device__ __forceinline__ void acc_scale2(Acc2 &A, f2x kk, f2x nk, f2x Z) {
+  const f2x p = rmul2(A.s, kk, Z);
+  const f2x e = fma2(A.s, kk, rmul2(A.s, nk, Z));  // A.s k - RN(A.s k), exact
+  A.c = fma2(A.c, kk, e);
+  A.s = p;
+}
+__device__ __forceinline__ P2 acc_get2(const Acc2 &A) {  // Fast2Sum(s, c)
+  P2 r;
+  r.h = add2(A.s, A.c);
+  r.l = sub2(A.c, sub2(r.h, A.s));
   return r;
 }
-// Neumaier-style accumulation of pairs: running (s, c), s the leading sum,
-// c the collected rounding errors and low parts.
-struct Acc {
-  float s, c;
-};
-__device__ __forceinline__ void acc_add(Acc &a, F2 v) {
-  float s, e;
-  two_sum(a.s, v.h, s, e);
-  a.s = s;
-  a.c += e + v.l;
-}
-__device__ __forceinline__ F2 acc_get(const Acc &a) { return fast_two_sum(a.s, a.c); }
-// pair times a small integer k (|k| < 2^24, exact as a float)
-__device__ __forceinline__ F2 mul_int(F2 a, float k) {
-  const float p = a.h * k;
-  float e = fmaf(a.h, k, -p);
-  e = fmaf(a.l, k, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ F2 mul_pair(F2 a, F2 b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ F2 add_pair(F2 a, F2 b) {
-  float s, e;
-  two_sum(a.h, b.h, s, e);
-  e += a.l + b.l;
-  return fast_two_sum(s, e);
-}
 
-// Exact split of a double into two floats (|x - hi - lo| <= 2^-48 |x|);
-// sets bad when |x| is outside [2^-74, 2^100] and not zero.
-__device__ __forceinline__ F2 split_double(double x, int &bad) {
+// Exact split of a double into two floats (|x - hi - lo| <= 2^-48 |x|) with
+// integer operations; (0, 0) for +-0, and (0, 0) with bad set when |x| is
+// outside [2^-74, 2^100].
+__device__ __forceinline__ void split_double(double x, float &h, float &l, int &bad) {
   const unsigned long long b = __double_as_longlong(x);
-  const unsigned hi32 = unsigned(b >> 32), lo32 = unsigned(b);
-  const int e = int((hi32 >> 20) & 0x7ffu);
-  const unsigned sgn = hi32 & 0x80000000u;
-  F2 r;
-  if (e == 0 && ((hi32 & 0xfffffu) | lo32) == 0u) {  // +-0
-    r.h = 0.0f;
-    r.l = 0.0f;
-    return r;
-  }
-  if (e < 1023 - 74 || e > 1023 + 100) {  // denormal, tiny, huge, inf, nan
-    bad = 1;
-    r.h = 0.0f;
-    r.l = 0.0f;
-    return r;
-  }
-  const unsigned mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
-  r.h = __int_as_float(int(sgn | (unsigned(e - 1023 + 127) << 23) | mh));
-  // remaining 29 bits, weight 2^(e - 1075): convert, then scale exactly
-  const unsigned rem = lo32 & 0x1fffffffu;
-  float l = __uint2float_rn(rem);                             // rounds 29 -> 24 bits
-  l *= __int_as_float(int(unsigned(e - 1075 + 127) << 23));  // 2^(e-1075) is a normal float
-  r.l = sgn ? -l : l;
-  return r;
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const unsigned t = hi & 0x7fffffffu;
+  const bool ok = (t - (949u << 20)) < (175u << 20);  // biased exponent in [949, 1123]
+  // float exponent e - 896 in [53, 227]; hi = leading 24 significand bits
+  const unsigned hb = __funnelshift_l(lo, t - (896u << 20), 3) | (hi & 0x80000000u);
+  // the next 29 bits, weight 2^(e - 1075) (a normal float for e >= 949)
+  const float w = __uint_as_float((hb & 0xff800000u) - (52u << 23));
+  const float lf = __uint2float_rn(lo & 0x1fffffffu) * w;
+  h = ok ? __uint_as_float(hb) : 0.0f;
+  l = ok ? lf : 0.0f;
+  bad |= int(!ok & ((t | lo) != 0u));
 }
 
-// Float -> double by bit re-biasing (no FP64 instruction).
-__device__ __forceinline__ double f2d_bits(float f, int extra_exp) {
+// Float -> double times 2^extra by re-biasing the exponent (no FP64
+// instruction); ebias = (1023 - 127 + extra) << 20.  Subnormal floats take
+// the FP64 conversion.
+__device__ __forceinline__ double f2d_bits(float f, unsigned ebias, int extra) {
   const unsigned u = __float_as_uint(f);
-  if ((u & 0x7fffffffu) == 0u) return 0.0;
-  if ((u & 0x7f800000u) == 0u) return ldexp(double(f), extra_exp);  // subnormal: rare, FP64 path
-  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  const long long e = (long long)((u >> 23) & 0xffu) - 127 + 1023 + extra_exp;
-  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | m));
+  if ((u & 0x7f800000u) == 0u) return (u & 0x7fffffffu) ? ldexp(double(f), extra) : 0.0;
+  const unsigned hi = ((u & 0x80000000u) | ((u >> 3) & 0x0fffffffu)) + ebias;
+  return __hiloint2double(int(hi), int(u << 29));
 }
 
 template <int NDIM>
-struct DfCfg;
+struct PkCfg;
 template <>
-struct DfCfg<2> {
-  static constexpr int VX = 4, TX = 256, TY = 1;
+struct PkCfg<2> {
+  static constexpr int TX = 256, TY = 1, VP = 2, PF = 4;
 };
 template <>
-struct DfCfg<3> {
-  static constexpr int VX = 4, TX = 16, TY = 16;
+struct PkCfg<3> {
+  static constexpr int TX = 16, TY = 16, VP = 2, PF = 2;
 };
 
-// One Laplacian pass t = L_int(x) in pair arithmetic over a streamed tile.
-// IN_PAIR: x is stored as float pairs (else doubles, split on arrival);
-// OUT_PAIR: t is stored as float pairs (else as the double scale * t).
-template <int NDIM, int R, bool IN_PAIR, bool OUT_PAIR>
-struct DfPass {
-  using C = DfCfg<NDIM>;
-  static constexpr int VX = C::VX, TX = C::TX, TY = C::TY, NTHR = TX * TY;
-  static constexpr int BX = TX * VX, BY = NDIM == 3 ? TY : 1;
+// PASS 1: doubles -> folded pair intermediate; PASS 2: folded pairs -> doubles.
+template <int NDIM, int R, int PASS>
+struct PkPass {
+  using C = PkCfg<NDIM>;
+  static constexpr int TX = C::TX, TY = C::TY, VP = C::VP, PF = C::PF, NTHR = TX * TY;
+  static constexpr int D = TX * VP;  // cells per tile row
+  static constexpr int HX = 2;       // x halo in cells (R <= 2)
   static constexpr int RP = NDIM == 3 ? R : 0;
-  static constexpr int HX = 2;  // stored x halo: R <= 2, two 8-byte elements per 16-byte chunk
-  static constexpr int PXS = BX + 2 * HX, PYS = BY + 2 * RP, PLANE = PXS * PYS;
-  static constexpr int PF = 2;            // planes in flight ahead of the one consumed
-  static constexpr int NR = R + 1 + PF;   // ring: R planes kept back for the in-plane terms
-  static constexpr int NQ = 2 * R + 1;    // register queue of centre values
-  static constexpr int NCHUNK = PLANE / 2;
-  static constexpr size_t SMEM = size_t(NR) * PLANE * 8;
+  static constexpr int BY = NDIM == 3 ? TY : 1;
+  static constexpr int PYS = BY + 2 * RP;
+  static constexpr int KS = D + 2 * HX;  // cells per smem row
+  static constexpr int FPLANE = KS * PYS;
+  // pass 1 stages raw doubles: two segments (lanes a and b) per row, each
+  // D + 2 HX values plus one spare 16-byte chunk for an odd half-row offset
+  static constexpr int SEG = D + 2 * HX + 2;
+  static constexpr int RPLANE = PASS == 1 ? 2 * SEG * PYS : 0;
+  static constexpr int NRAW = PASS == 1 ? PF + 1 : 0;
+  static constexpr int NRAWM = NRAW > 0 ? NRAW : 1;  // ring index modulus
+  static constexpr int NF = PASS == 1 ? R + 1 : R + 1 + PF;  // folded planes in smem
+  static constexpr int NQ = 2 * R + 1;                      // register queue of centre cells
+  static constexpr int NCH = PASS == 1 ? PYS * SEG : FPLANE; // 16-byte copies per plane
+  static constexpr int NCPT = (NCH + NTHR - 1) / NTHR;
+  static constexpr int NFPT = (FPLANE + NTHR - 1) / NTHR;    // fold work per thread (pass 1)
+  static constexpr size_t SMEM = size_t(NRAW) * RPLANE * 8 + size_t(NF) * FPLANE * 16;
 };
 
-struct DfGeom {
-  int nx, ny, nz;  // output dims (nz = 1 in 2D)
-  int bc;          // BC_PERIODIC or BC_GHOSTED (input ring R)
-  int H;
-  long long in_sy, in_ss, out_sy, out_ss;
-  float c0, c1, c2;  // integer weights: centre (all axes), distance 1, distance 2
-  F2 scale;          // OUT double: scale' in [1, 2) as a pair ...
-  int scale_exp;     // ... times 2^scale_exp
+struct PkGeom {
+  int nx, ny, nz;   // output grid (nz = 1 in 2D)
+  int nf, nc;       // folded row length (even) and its cells nf / 2
+  int off_out;      // pass 2: output x = fold position - off_out
+  int bc;           // BC_PERIODIC or BC_GHOSTED (input ring R) on y/z (and on x of pass 1)
+  int H;            // output planes per CTA
+  long long in_sy, in_ss;    // input strides (pass 1: doubles, pass 2: cells)
+  long long out_sy, out_ss;  // output strides (pass 1: cells, pass 2: doubles)
+  float c0, c1, c2;          // integer weights
+  float zero;                // 0.0f (see rmul2)
+  float sh, sl;              // pass 2: scale mantissa in [1, 2) as an exact float pair ...
+  int sexp;                  // ... times 2^sexp
 };
 
-template <int NDIM, int R, bool IN_PAIR, bool OUT_PAIR>
-__global__ void __launch_bounds__(DfPass<NDIM, R, IN_PAIR, OUT_PAIR>::NTHR)
-    df_lap_kernel(const void *__restrict__ xin, void *__restrict__ yout, DfGeom g, int *__restrict__ bad_flag) {
-  using K = DfPass<NDIM, R, IN_PAIR, OUT_PAIR>;
+template <int NDIM, int R, int PASS>
+__global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
+    pk_lap_kernel(const void *__restrict__ xin, void *__restrict__ yout, PkGeom g, int *__restrict__ bad_flag) {
+  using K = PkPass<NDIM, R, PASS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // ring of planes, 8 bytes per element (a double, or a float pair once split)
-  unsigned long long *ring = reinterpret_cast<unsigned long long *>(smem_raw);
-  const int tx = threadIdx.x % K::TX, ty = threadIdx.x / K::TX;
-  const int x0 = blockIdx.x * K::BX;
+  ulonglong2 *fold = reinterpret_cast<ulonglong2 *>(smem_raw + size_t(K::NRAW) * K::RPLANE * 8);
+  const unsigned long long *raw = reinterpret_cast<const unsigned long long *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tx = tid % K::TX, ty = tid / K::TX;
+  const int k0 = blockIdx.x * K::D;  // first cell of the tile
   const int y0 = NDIM == 3 ? blockIdx.y * K::BY : 0;
   const int z0 = (NDIM == 3 ? blockIdx.z : blockIdx.y) * g.H;
   const int ns = NDIM == 3 ? g.nz : g.ny;
   const int zend = min(z0 + g.H, ns);
   const int NT = (zend - z0) + 2 * R;
-  const unsigned long long *src = static_cast<const unsigned long long *>(xin);
+  const long long in_ps = NDIM == 3 ? g.in_ss : g.in_sy;
   int bad = 0;
 
-  auto load_plane = [&](int t) {
-    const int zs = z0 - R + t;
-    const int iz = map_coord(zs, ns, g.bc, R);
-    unsigned long long *buf = ring + (t % K::NR) * K::PLANE;
-    const long long pbase = (long long)iz * (NDIM == 3 ? g.in_ss : g.in_sy);
-    for (int c = threadIdx.x; c < K::NCHUNK; c += K::NTHR) {
-      const int e = c * 2, r = e / K::PXS, cc = e - r * K::PXS;
-      const int ix = map_coord(x0 - K::HX + cc, g.nx, g.bc, R);
+  // In-plane source offsets of this thread's 16-byte copies (fixed for the
+  // CTA); -1: zero fill.  Pass 2 also notes the cells whose lanes are swapped.
+  int src_off[K::NCPT];
+  unsigned swap_mask = 0;
+  const int ob = g.nc & 1;
+#pragma unroll
+  for (int i = 0; i < K::NCPT; ++i) {
+    const int ch = tid + i * K::NTHR;
+    src_off[i] = -1;
+    if (ch >= K::NCH) continue;
+    if (PASS == 1) {
+      const int r = ch / K::SEG, rem = ch - r * K::SEG;  // SEG/2 chunks per segment row
+      const int gsel = rem / (K::SEG / 2), j = rem - gsel * (K::SEG / 2);
+      const int p = (gsel ? k0 + g.nc - K::HX - ob : k0 - K::HX) + 2 * j;
+      const int ix = map_coord(p, g.nf, g.bc, R);
       int iy = 0;
       if (NDIM == 3) iy = map_coord(y0 - K::RP + r, g.ny, g.bc, R);
-      const bool ok = (iz >= 0) & (ix >= 0) & (iy >= 0);
-      const unsigned long long *s = ok ? src + pbase + (long long)iy * g.in_sy + ix : src;
-      cp_async16(buf + e, s, ok ? 16 : 0);
+      if (ix >= 0 && iy >= 0) src_off[i] = int((long long)iy * g.in_sy + ix);
+    } else {
+      const int r = ch / K::KS, c = ch - r * K::KS;
+      int gc = k0 - K::HX + c;
+      bool sw = false;
+      if (gc < 0) {
+        gc += g.nc;
+        sw = true;
+      } else if (gc >= g.nc) {
+        gc -= g.nc;
+        sw = true;
+      }
+      int iy = 0;
+      if (NDIM == 3) iy = map_coord(y0 - K::RP + r, g.ny, g.bc, R);
+      if (gc >= 0 && gc < g.nc && iy >= 0) {
+        src_off[i] = int((long long)iy * g.in_sy + gc);
+        if (sw) swap_mask |= 1u << i;
+      }
+    }
+  }
+
+  auto load_plane = [&](int t) {
+    const int iz = map_coord(z0 - R + t, ns, g.bc, R);
+    const long long pb = (long long)iz * in_ps;
+#pragma unroll
+    for (int i = 0; i < K::NCPT; ++i) {
+      const int ch = tid + i * K::NTHR;
+      if (ch >= K::NCH) continue;
+      const bool ok = iz >= 0 && src_off[i] >= 0;
+      if (PASS == 1) {
+        unsigned long long *dst = const_cast<unsigned long long *>(raw) + size_t(t % K::NRAWM) * K::RPLANE + 2 * ch;
+        const unsigned long long *src = static_cast<const unsigned long long *>(xin) + (ok ? pb + src_off[i] : 0);
+        cp_async16(dst, src, ok ? 16 : 0);
+      } else {
+        ulonglong2 *dst = fold + size_t(t % K::NF) * K::FPLANE + ch;
+        const ulonglong2 *src = static_cast<const ulonglong2 *>(xin) + (ok ? pb + src_off[i] : 0);
+        cp_async16(dst, src, ok ? 16 : 0);
+      }
     }
   };
 
-  F2 q[K::NQ][K::VX];
+  const f2x kc0 = pk2(g.c0, g.c0), nc0 = pk2(-g.c0, -g.c0);
+  const f2x kc1 = pk2(g.c1, g.c1), nc1 = pk2(-g.c1, -g.c1);
+  const f2x kc2 = pk2(g.c2, g.c2), nc2 = pk2(-g.c2, -g.c2);
+  const f2x Z = pk2(g.zero, g.zero);
+  const int row = NDIM == 3 ? ty + K::RP : 0;
+  const int col = tx * K::VP + K::HX;  // smem cell of the first owned cell
+  const int yy = y0 + ty;
+  P2 q[K::NQ][K::VP];
+
 #pragma unroll
   for (int k = 0; k < K::PF; ++k) {
     if (k < NT) load_plane(k);
     cp_async_commit();
   }
-  const int xo = x0 + tx * K::VX;
-  const int yy = y0 + ty;
-  const int col = tx * K::VX + K::HX;         // smem column of the first owned point
-  const int row = NDIM == 3 ? ty + K::RP : 0;  // smem row of the owned points
   for (int tb = 0; tb < NT; tb += K::NQ) {
 #pragma unroll
     for (int s = 0; s < K::NQ; ++s) {
       const int t = tb + s;
       if (t >= NT) break;
       cp_async_wait<K::PF - 1>();
+      ulonglong2 *fp = fold + size_t(t % K::NF) * K::FPLANE;
+      if (PASS == 2 && swap_mask) {  // own copies have landed: swap the wrapped cells' lanes
+#pragma unroll
+        for (int i = 0; i < K::NCPT; ++i)
+          if (swap_mask & (1u << i)) {
+            ulonglong2 v = fp[tid + i * K::NTHR];
+            float a, b;
+            upk2(v.x, a, b);
+            v.x = pk2(b, a);
+            upk2(v.y, a, b);
+            v.y = pk2(b, a);
+            fp[tid + i * K::NTHR] = v;
+          }
+      }
       __syncthreads();
       if (t + K::PF < NT) load_plane(t + K::PF);
       cp_async_commit();
-      unsigned long long *pl = ring + (t % K::NR) * K::PLANE;
-      if (!IN_PAIR) {  // split the arrived doubles into pairs, in place
-        for (int e = threadIdx.x; e < K::PLANE; e += K::NTHR) {
-          const F2 v = split_double(__longlong_as_double((long long)pl[e]), bad);
-          pl[e] = (unsigned long long)__float_as_uint(v.h) | ((unsigned long long)__float_as_uint(v.l) << 32);
+      if (PASS == 1) {  // split and fold the arrived doubles
+        const unsigned long long *rp = raw + size_t(t % K::NRAWM) * K::RPLANE;
+#pragma unroll
+        for (int i = 0; i < K::NFPT; ++i) {
+          const int f = tid + i * K::NTHR;
+          if (f >= K::FPLANE) continue;
+          const int r = f / K::KS, c = f - r * K::KS;
+          const double va = __longlong_as_double((long long)rp[(2 * r) * K::SEG + c]);
+          const double vb = __longlong_as_double((long long)rp[(2 * r + 1) * K::SEG + c + ob]);
+          float ha, la, hb, lb;
+          split_double(va, ha, la, bad);
+          split_double(vb, hb, lb, bad);
+          fp[f] = make_ulonglong2(pk2(ha, hb), pk2(la, lb));
         }
         __syncthreads();
       }
-      const F2 *pf = reinterpret_cast<const F2 *>(pl);
-      // centre values of this plane into the queue
+      // centre cells of this plane into the queue
 #pragma unroll
-      for (int v = 0; v < K::VX; ++v) q[s][v] = pf[row * K::PXS + col + v];
-      if (t >= 2 * R) {
-        // output plane z0 + t - 2R: in-plane terms from the plane R back,
-        // streaming-axis terms from the queue
-        const F2 *pc = reinterpret_cast<const F2 *>(ring + ((t - R) % K::NR) * K::PLANE);
-        const int j = z0 + t - 2 * R;
-        const int sc_ = ((s - R) % K::NQ + K::NQ) % K::NQ;
-        F2 seg[K::VX + 2 * R];
+      for (int v = 0; v < K::VP; ++v) {
+        const ulonglong2 c = fp[row * K::KS + col + v];
+        q[s][v].h = c.x;
+        q[s][v].l = c.y;
+      }
+      if (t < 2 * R) continue;
+      // output plane z0 + t - 2R: in-plane terms from the plane R back,
+      // streaming-axis terms from the queue
+      const ulonglong2 *pc = fold + size_t((t - R) % K::NF) * K::FPLANE;
+      const int j = z0 + t - 2 * R;
+      ulonglong2 seg[K::VP + 2 * R];
 #pragma unroll
-        for (int i = 0; i < K::VX + 2 * R; ++i) seg[i] = pc[row * K::PXS + col - R + i];
-        F2 out[K::VX];
+      for (int i = 0; i < K::VP + 2 * R; ++i) seg[i] = pc[row * K::KS + col - R + i];
+      P2 out[K::VP];
 #pragma unroll
-        for (int v = 0; v < K::VX; ++v) {
-          Acc a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
-          acc_add(a1, seg[v + R - 1]);
-          acc_add(a1, seg[v + R + 1]);
-          acc_add(a1, q[((s - R - 1) % K::NQ + K::NQ) % K::NQ][v]);
-          acc_add(a1, q[((s - R + 1) % K::NQ + K::NQ) % K::NQ][v]);
-          if (NDIM == 3) {
-            acc_add(a1, pc[(row - 1) * K::PXS + col + v]);
-            acc_add(a1, pc[(row + 1) * K::PXS + col + v]);
-          }
-          F2 t1 = mul_int(acc_get(a1), g.c1);
-          F2 tc = mul_int(q[sc_][v], g.c0);
-          F2 r = add_pair(t1, tc);
-          if (R == 2) {
-            acc_add(a2, seg[v + R - 2]);
-            acc_add(a2, seg[v + R + 2]);
-            acc_add(a2, q[((s - R - 2) % K::NQ + K::NQ) % K::NQ][v]);
-            acc_add(a2, q[((s - R + 2) % K::NQ + K::NQ) % K::NQ][v]);
-            if (NDIM == 3) {
-              acc_add(a2, pc[(row - 2) * K::PXS + col + v]);
-              acc_add(a2, pc[(row + 2) * K::PXS + col + v]);
-            }
-            r = add_pair(r, mul_int(acc_get(a2), g.c2));
-          }
-          out[v] = r;
+      for (int v = 0; v < K::VP; ++v) {
+        const P2 &zm1 = q[(s - R - 1 + 2 * K::NQ) % K::NQ][v];
+        const P2 &zp1 = q[(s - R + 1 + 2 * K::NQ) % K::NQ][v];
+        const P2 &ctr = q[(s - R + 2 * K::NQ) % K::NQ][v];
+        Acc2 A{seg[v + R - 1].x, seg[v + R - 1].y};
+        acc_add2(A, seg[v + R + 1].x, seg[v + R + 1].y);
+        acc_add2(A, zm1.h, zm1.l);
+        acc_add2(A, zp1.h, zp1.l);
+        if (NDIM == 3) {
+          const ulonglong2 a = pc[(row - 1) * K::KS + col + v], b = pc[(row + 1) * K::KS + col + v];
+          acc_add2(A, a.x, a.y);
+          acc_add2(A, b.x, b.y);
         }
-        if (j < zend && (NDIM == 2 || yy < g.ny)) {
-          const long long base = (long long)j * (NDIM == 3 ? g.out_ss : g.out_sy) +
-                                 (NDIM == 3 ? (long long)yy * g.out_sy : 0) + xo;
-#pragma unroll
-          for (int v = 0; v < K::VX; ++v) {
-            if (xo + v >= g.nx) continue;
-            if (OUT_PAIR) {
-              reinterpret_cast<F2 *>(yout)[base + v] = out[v];
-            } else {
-              const F2 z = mul_pair(out[v], g.scale);  // |scale| in [1, 2): no overflow
-              // exact: the pair's 48 significant bits fit a double
-              const double d = f2d_bits(z.h, g.scale_exp) + f2d_bits(z.l, g.scale_exp);
-              static_cast<double *>(yout)[base + v] = d;
-            }
+        acc_scale2(A, kc1, nc1, Z);
+        {  // centre: TwoProduct of c0 * hi, plus c0 * lo
+          const f2x p = rmul2(ctr.h, kc0, Z);
+          f2x e = fma2(ctr.h, kc0, rmul2(ctr.h, nc0, Z));
+          e = fma2(ctr.l, kc0, e);
+          acc_add2(A, p, e);
+        }
+        if (R == 2) {
+          const P2 &zm2 = q[(s - R - 2 + 2 * K::NQ) % K::NQ][v];
+          const P2 &zp2 = q[(s - R + 2 + 2 * K::NQ) % K::NQ][v];
+          Acc2 B{seg[v].x, seg[v].y};
+          acc_add2(B, seg[v + 4].x, seg[v + 4].y);
+          acc_add2(B, zm2.h, zm2.l);
+          acc_add2(B, zp2.h, zp2.l);
+          if (NDIM == 3) {
+            const ulonglong2 a = pc[(row - 2) * K::KS + col + v], b = pc[(row + 2) * K::KS + col + v];
+            acc_add2(B, a.x, a.y);
+            acc_add2(B, b.x, b.y);
           }
+          acc_scale2(B, kc2, nc2, Z);
+          acc_add2(A, B.s, B.c);
+        }
+        out[v] = acc_get2(A);
+      }
+      if (j >= zend || (NDIM == 3 && yy >= g.ny)) continue;
+      const long long obase = (long long)j * (NDIM == 3 ? g.out_ss : g.out_sy) + (NDIM == 3 ? (long long)yy * g.out_sy : 0);
+      if (PASS == 1) {
+#pragma unroll
+        for (int v = 0; v < K::VP; ++v) {
+          const int cell = k0 + tx * K::VP + v;
+          if (cell < g.nc) reinterpret_cast<ulonglong2 *>(yout)[obase + cell] = make_ulonglong2(out[v].h, out[v].l);
+        }
+      } else {
+        const f2x sh = pk2(g.sh, g.sh), nsh = pk2(-g.sh, -g.sh), sl = pk2(g.sl, g.sl);
+        const unsigned ebias = unsigned(1023 - 127 + g.sexp) << 20;
+        double da[K::VP], db[K::VP];
+#pragma unroll
+        for (int v = 0; v < K::VP; ++v) {
+          // z = out * scale (TwoProduct, |scale| in [1, 2): no overflow), then
+          // the pair's 48 significant bits rebuilt exactly as a double
+          const f2x p = rmul2(out[v].h, sh, Z);
+          f2x e = fma2(out[v].h, sh, rmul2(out[v].h, nsh, Z));
+          e = fma2(out[v].h, sl, e);
+          e = fma2(out[v].l, sh, e);
+          const f2x zh = add2(p, e);
+          const f2x zl = sub2(e, sub2(zh, p));
+          float ha, hb, la, lb;
+          upk2(zh, ha, hb);
+          upk2(zl, la, lb);
+          da[v] = f2d_bits(ha, ebias, g.sexp) + f2d_bits(la, ebias, g.sexp);
+          db[v] = f2d_bits(hb, ebias, g.sexp) + f2d_bits(lb, ebias, g.sexp);
+        }
+        double *yo = static_cast<double *>(yout) + obase;
+        const int xa = k0 + tx * K::VP - g.off_out, xb = xa + g.nc;
+#pragma unroll
+        for (int v = 0; v < K::VP; ++v) {
+          if (k0 + tx * K::VP + v >= g.nc) continue;
+          if (xa + v >= 0 && xa + v < g.nx) yo[xa + v] = da[v];
+          if (xb + v >= 0 && xb + v < g.nx) yo[xb + v] = db[v];
         }
       }
     }
@@ -285,7 +420,6 @@ __global__ void __launch_bounds__(DfPass<NDIM, R, IN_PAIR, OUT_PAIR>::NTHR)
   cp_async_wait<0>();
   if (bad) atomicOr(bad_flag, 1);
 }
-
 // ---------------------------------------------------------------------------
 
 // Integer form of a symmetric star stencil: centre c0 (all axes), c1 at
@@ -325,35 +459,49 @@ bool star_int_form(const sc_stencil *s, float *c0, float *c1, float *c2) {
   return true;
 }
 
-template <int NDIM, int R, bool IN_PAIR, bool OUT_PAIR>
-static int launch_df(const void *x, void *y, const int64_t *dims, int bc, float c0, float c1, float c2,
-                     double scale, int *flag, cudaStream_t st, int planes) {
-  using K = DfPass<NDIM, R, IN_PAIR, OUT_PAIR>;
-  DfGeom g;
+
+template <int NDIM, int R, int PASS>
+static int launch_pk(const void *x, void *y, const int64_t *dims, int bc, const float *c, double scale, int *flag,
+                     cudaStream_t st, int planes) {
+  using K = PkPass<NDIM, R, PASS>;
+  PkGeom g;
   std::memset(&g, 0, sizeof(g));
   g.nx = int(dims[0]);
   g.ny = int(dims[1]);
   g.nz = NDIM == 3 ? int(dims[2]) : 1;
   g.bc = bc == SC_BC_GHOSTED ? BC_GHOSTED : BC_PERIODIC;
   const int sh = bc == SC_BC_GHOSTED ? 2 * R : 0;
-  g.in_sy = g.nx + sh;
-  g.in_ss = (long long)(g.nx + sh) * (g.ny + sh);
-  g.out_sy = g.nx;
-  g.out_ss = (long long)g.nx * g.ny;
-  g.c0 = c0;
-  g.c1 = c1;
-  g.c2 = c2;
-  if (!OUT_PAIR) {  // scale = m * 2^e, m in [1, 2), m as an exact pair of floats
+  // pass 1 folds its output rows (length nx); pass 2 folds its input rows
+  // (length nx + 2R when ghosted) and writes the points that are outputs
+  g.nf = PASS == 1 ? g.nx : g.nx + sh;
+  g.nc = g.nf / 2;
+  g.off_out = PASS == 1 ? 0 : sh / 2;
+  const long long in_rows = (long long)g.ny + sh;
+  if (PASS == 1) {
+    g.in_sy = g.nx + sh;
+    g.in_ss = (long long)(g.nx + sh) * in_rows;
+    g.out_sy = g.nc;
+    g.out_ss = (long long)g.nc * g.ny;
+  } else {
+    g.in_sy = g.nc;
+    g.in_ss = (long long)g.nc * in_rows;
+    g.out_sy = g.nx;
+    g.out_ss = (long long)g.nx * g.ny;
+  }
+  g.c0 = c[0];
+  g.c1 = c[1];
+  g.c2 = c[2];
+  if (PASS == 2) {  // scale = m * 2^e, m in [1, 2), m as an exact pair of floats
     int e = 0;
     const double m = std::frexp(scale, &e) * 2.0;
-    g.scale_exp = e - 1;
-    const float mh = float(m);
-    g.scale.h = mh;
-    g.scale.l = float(m - double(mh));
+    g.sexp = e - 1;
+    g.sh = float(m);
+    g.sl = float(m - double(g.sh));
   }
   const int ns = NDIM == 3 ? g.nz : g.ny;
-  const long long txy = (long long)((g.nx + K::BX - 1) / K::BX) * (NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : 1);
-  auto kern = df_lap_kernel<NDIM, R, IN_PAIR, OUT_PAIR>;
+  const int gx = (g.nc + K::D - 1) / K::D;
+  const long long txy = (long long)gx * (NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : 1);
+  auto kern = pk_lap_kernel<NDIM, R, PASS>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
@@ -363,8 +511,7 @@ static int launch_df(const void *x, void *y, const int64_t *dims, int bc, float 
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, K::NTHR, K::SMEM);
   g.H = planes > 0 ? std::min(planes, ns)
                    : wave_planes(txy, ns, R, (long long)std::max(occ, 1) * num_sms(), std::max(4 * R, 8));
-  dim3 grid((g.nx + K::BX - 1) / K::BX, NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : (ns + g.H - 1) / g.H,
-            NDIM == 3 ? (ns + g.H - 1) / g.H : 1);
+  dim3 grid(gx, NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : (ns + g.H - 1) / g.H, NDIM == 3 ? (ns + g.H - 1) / g.H : 1);
   kern<<<grid, K::NTHR, K::SMEM, st>>>(x, y, g, flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SC_ECUDA, "pair-arithmetic apply launch: %s", cudaGetErrorString(e));
@@ -372,21 +519,37 @@ static int launch_df(const void *x, void *y, const int64_t *dims, int bc, float 
 }
 
 template <int NDIM, int R>
-static int df_two_passes(const void *x, void *t, void *y, const int64_t *dims_t, const int64_t *dims_y, int bc,
+static int pk_two_passes(const void *x, void *t, void *y, const int64_t *dims_t, const int64_t *dims_y, int bc,
                          const float *ca, const float *cb, double scale, int *flag, cudaStream_t st, int planes) {
-  if (int rc = launch_df<NDIM, R, false, true>(x, t, dims_t, bc, ca[0], ca[1], ca[2], 1.0, flag, st, planes))
-    return rc;
-  return launch_df<NDIM, R, true, false>(t, y, dims_y, bc, cb[0], cb[1], cb[2], scale, flag, st, planes);
+  if (int rc = launch_pk<NDIM, R, 1>(x, t, dims_t, bc, ca, 1.0, flag, st, planes)) return rc;
+  return launch_pk<NDIM, R, 2>(t, y, dims_y, bc, cb, scale, flag, st, planes);
+}
+
+bool df_supported(int ndim, int R, const int64_t *dims_y, int bc, double scale, const void *x, const void *t,
+                  const void *y) {
+  if (ndim < 2 || ndim > 3 || R < 1 || R > 2) return false;
+  if (bc != SC_BC_PERIODIC && !(bc == SC_BC_GHOSTED && R == 2)) return false;
+  if (dims_y[0] % 2 != 0 || dims_y[0] < 4) return false;
+  if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(t) | reinterpret_cast<uintptr_t>(y)) & 15) != 0)
+    return false;
+  // the result's exponent stays inside the double range after re-biasing
+  int e = 0;
+  std::frexp(scale, &e);
+  if (!(scale > 0.0) || e < -800 || e > 800) return false;
+  // in-plane offsets are 32-bit
+  const long long sh = bc == SC_BC_GHOSTED ? 4 * R : 0;
+  const long long plane = ndim == 3 ? (dims_y[0] + sh) * (dims_y[1] + sh) : dims_y[0] + sh;
+  return plane < (1LL << 31);
 }
 
 int df_composition_enqueue(int ndim, int R, const void *x, void *t, void *y, const int64_t *dims_t,
                            const int64_t *dims_y, int bc, const float *ca, const float *cb, double scale,
                            int *flag, cudaStream_t st, int planes) {
   if (ndim == 2)
-    return R == 1 ? df_two_passes<2, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes)
-                  : df_two_passes<2, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes);
-  return R == 1 ? df_two_passes<3, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes)
-                : df_two_passes<3, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes);
+    return R == 1 ? pk_two_passes<2, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes)
+                  : pk_two_passes<2, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes);
+  return R == 1 ? pk_two_passes<3, 1>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes)
+                : pk_two_passes<3, 2>(x, t, y, dims_t, dims_y, bc, ca, cb, scale, flag, st, planes);
 }
 
 }  // namespace sc

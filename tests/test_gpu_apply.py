@@ -214,7 +214,8 @@ def test_star_stencils_use_star_class():
 
 
 PAIR_CASES = [(2, 4, (8192, 40)), (2, 2, (1100, 301)), (2, 4, (1101, 97)), (3, 4, (150, 40, 37)),
-              (3, 2, (64, 20, 30)), (3, 4, (68, 33, 17))]
+              (3, 2, (64, 20, 30)), (3, 4, (68, 33, 17)), (2, 4, (6, 9)), (2, 4, (1102, 17)),
+              (3, 4, (12, 10, 9)), (3, 2, (4, 5, 6))]
 
 
 def _nested_check(L, oL, x, yt, bc, n, elem_tol):
@@ -245,8 +246,15 @@ def test_pair_arithmetic_fp64_matches_oracle(ndim, order, dims, bc):
     x = fields.uniform(xshape, seed=zlib.crc32(repr(("pair", ndim, order, dims, bc)).encode()))
     yt = torch.full(shape, float("nan"), dtype=torch.float64, device=DEV)
     sc.apply_composition(L, L, torch.from_numpy(x).to(DEV), yt, bc=bc, h=(1, n), dims=dims, arith="pair")
+    yn = torch.full(shape, float("nan"), dtype=torch.float64, device=DEV)
+    sc.apply_composition(L, L, torch.from_numpy(x).to(DEV), yn, bc=bc, h=(1, n), dims=dims, arith="native")
     torch.cuda.synchronize()
     _nested_check(L, oL, x, yt, bc, n, 2.0 ** -42)
+    # even rows take the pair passes (their rounding differs from the native
+    # nested passes somewhere), as long as the boundary is periodic or the
+    # factors have radius 2; otherwise exactly the native passes run
+    paired = n % 2 == 0 and (bc == "periodic" or oL.radius == 2)
+    assert torch.equal(yt, yn) != paired
 
 
 def test_pair_arithmetic_out_of_range_inputs_fall_back():
