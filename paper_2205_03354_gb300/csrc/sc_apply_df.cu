@@ -109,6 +109,22 @@ __device__ __forceinline__ void acc_scale2(Acc2 &A, f2x kk, f2x nk, f2x Z) {
   A.c = fma2(A.c, kk, e);
   A.s = p;
 }
+// (a_h + a_l) + (b_h + b_l) as an unnormalised accumulator: TwoSum of the
+// leading parts, the low parts and the rounding error collected.
+__device__ __forceinline__ Acc2 pair_sum2(f2x ah, f2x al, f2x bh, f2x bl) {
+  const f2x s = add2(ah, bh);
+  const f2x bb = sub2(s, ah);
+  const f2x e = add2(sub2(ah, sub2(s, bb)), sub2(bh, bb));
+  return Acc2{s, add2(e, add2(al, bl))};
+}
+// A -= B (TwoSum of A.s and -B.s, compensations subtracted)
+__device__ __forceinline__ void acc_sub2(Acc2 &A, const Acc2 &B) {
+  const f2x s = sub2(A.s, B.s);
+  const f2x bb = sub2(s, A.s);
+  const f2x e = sub2(sub2(A.s, sub2(s, bb)), add2(B.s, bb));
+  A.s = s;
+  A.c = add2(A.c, sub2(e, B.c));
+}
 __device__ __forceinline__ P2 acc_get2(const Acc2 &A) {  // Fast2Sum(s, c)
   P2 r;
   r.h = add2(A.s, A.c);
@@ -135,12 +151,13 @@ __device__ __forceinline__ void split_double(double x, float &h, float &l, int &
 }
 
 // Float -> double times 2^extra by re-biasing the exponent (no FP64
-// instruction); ebias = (1023 - 127 + extra) << 20.  Subnormal floats take
-// the FP64 conversion.
-__device__ __forceinline__ double f2d_bits(float f, unsigned ebias, int extra) {
+// instruction); ebias = (1023 - 127 + extra) << 20.  Zero maps to zero; a
+// subnormal float sets bad (the native passes then recompute the result).
+__device__ __forceinline__ double f2d_bits(float f, unsigned ebias, int &bad) {
   const unsigned u = __float_as_uint(f);
-  if ((u & 0x7f800000u) == 0u) return (u & 0x7fffffffu) ? ldexp(double(f), extra) : 0.0;
-  const unsigned hi = ((u & 0x80000000u) | ((u >> 3) & 0x0fffffffu)) + ebias;
+  const unsigned a = u & 0x7fffffffu, sg = u & 0x80000000u;
+  const unsigned hi = a ? (sg | (a >> 3)) + ebias : sg;
+  bad |= int(a != 0u && a < 0x00800000u);
   return __hiloint2double(int(hi), int(u << 29));
 }
 
@@ -181,6 +198,8 @@ struct PkPass {
   static constexpr size_t SMEM = size_t(NRAW) * RPLANE * 8 + size_t(NF) * FPLANE * 16;
 };
 
+enum { PK_C1_POW2 = 1, PK_C2_POW2 = 2, PK_C2_MINUS1 = 4 };
+
 struct PkGeom {
   int nx, ny, nz;   // output grid (nz = 1 in 2D)
   int nf, nc;       // folded row length (even) and its cells nf / 2
@@ -191,12 +210,13 @@ struct PkGeom {
   long long out_sy, out_ss;  // output strides (pass 1: cells, pass 2: doubles)
   float c0, c1, c2;          // integer weights
   float zero;                // 0.0f (see rmul2)
+  int flags;                 // PK_* properties of the weights
   float sh, sl;              // pass 2: scale mantissa in [1, 2) as an exact float pair ...
   int sexp;                  // ... times 2^sexp
 };
 
 template <int NDIM, int R, int PASS>
-__global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
+__global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2)
     pk_lap_kernel(const void *__restrict__ xin, void *__restrict__ yout, PkGeom g, int *__restrict__ bad_flag) {
   using K = PkPass<NDIM, R, PASS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -276,7 +296,9 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
   const f2x kc2 = pk2(g.c2, g.c2), nc2 = pk2(-g.c2, -g.c2);
   const f2x Z = pk2(g.zero, g.zero);
   const int row = NDIM == 3 ? ty + K::RP : 0;
-  const int col = tx * K::VP + K::HX;  // smem cell of the first owned cell
+  // owned cells tx + v TX (v < VP): consecutive lanes read consecutive
+  // 16-byte cells, free of shared-memory bank conflicts
+  const int col = tx + K::HX;  // smem cell of the first owned cell
   const int yy = y0 + ty;
   P2 q[K::NQ][K::VP];
 
@@ -327,7 +349,7 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
       // centre cells of this plane into the queue
 #pragma unroll
       for (int v = 0; v < K::VP; ++v) {
-        const ulonglong2 c = fp[row * K::KS + col + v];
+        const ulonglong2 c = fp[row * K::KS + col + v * K::TX];
         q[s][v].h = c.x;
         q[s][v].l = c.y;
       }
@@ -336,25 +358,29 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
       // streaming-axis terms from the queue
       const ulonglong2 *pc = fold + size_t((t - R) % K::NF) * K::FPLANE;
       const int j = z0 + t - 2 * R;
-      ulonglong2 seg[K::VP + 2 * R];
-#pragma unroll
-      for (int i = 0; i < K::VP + 2 * R; ++i) seg[i] = pc[row * K::KS + col - R + i];
       P2 out[K::VP];
 #pragma unroll
       for (int v = 0; v < K::VP; ++v) {
         const P2 &zm1 = q[(s - R - 1 + 2 * K::NQ) % K::NQ][v];
         const P2 &zp1 = q[(s - R + 1 + 2 * K::NQ) % K::NQ][v];
         const P2 &ctr = q[(s - R + 2 * K::NQ) % K::NQ][v];
-        Acc2 A{seg[v + R - 1].x, seg[v + R - 1].y};
-        acc_add2(A, seg[v + R + 1].x, seg[v + R + 1].y);
-        acc_add2(A, zm1.h, zm1.l);
-        acc_add2(A, zp1.h, zp1.l);
+        const ulonglong2 *pr = pc + row * K::KS + col + v * K::TX;  // this cell, plane t - R
+        // distance-1 sum as a tree of pair sums (short dependency chains)
+        const ulonglong2 xm1 = pr[-1], xp1 = pr[1];
+        Acc2 A = pair_sum2(xm1.x, xm1.y, xp1.x, xp1.y);
+        Acc2 Az = pair_sum2(zm1.h, zm1.l, zp1.h, zp1.l);
         if (NDIM == 3) {
-          const ulonglong2 a = pc[(row - 1) * K::KS + col + v], b = pc[(row + 1) * K::KS + col + v];
-          acc_add2(A, a.x, a.y);
-          acc_add2(A, b.x, b.y);
+          const ulonglong2 a = pr[-K::KS], b = pr[K::KS];
+          const Acc2 Ay = pair_sum2(a.x, a.y, b.x, b.y);
+          acc_add2(Az, Ay.s, Ay.c);
         }
-        acc_scale2(A, kc1, nc1, Z);
+        acc_add2(A, Az.s, Az.c);
+        if (g.flags & PK_C1_POW2) {  // exact scaling
+          A.s = rmul2(A.s, kc1, Z);
+          A.c = rmul2(A.c, kc1, Z);
+        } else {
+          acc_scale2(A, kc1, nc1, Z);
+        }
         {  // centre: TwoProduct of c0 * hi, plus c0 * lo
           const f2x p = rmul2(ctr.h, kc0, Z);
           f2x e = fma2(ctr.h, kc0, rmul2(ctr.h, nc0, Z));
@@ -364,17 +390,26 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
         if (R == 2) {
           const P2 &zm2 = q[(s - R - 2 + 2 * K::NQ) % K::NQ][v];
           const P2 &zp2 = q[(s - R + 2 + 2 * K::NQ) % K::NQ][v];
-          Acc2 B{seg[v].x, seg[v].y};
-          acc_add2(B, seg[v + 4].x, seg[v + 4].y);
-          acc_add2(B, zm2.h, zm2.l);
-          acc_add2(B, zp2.h, zp2.l);
+          const ulonglong2 xm2 = pr[-2], xp2 = pr[2];
+          Acc2 B = pair_sum2(xm2.x, xm2.y, xp2.x, xp2.y);
+          Acc2 Bz = pair_sum2(zm2.h, zm2.l, zp2.h, zp2.l);
           if (NDIM == 3) {
-            const ulonglong2 a = pc[(row - 2) * K::KS + col + v], b = pc[(row + 2) * K::KS + col + v];
-            acc_add2(B, a.x, a.y);
-            acc_add2(B, b.x, b.y);
+            const ulonglong2 a = pr[-2 * K::KS], b = pr[2 * K::KS];
+            const Acc2 By = pair_sum2(a.x, a.y, b.x, b.y);
+            acc_add2(Bz, By.s, By.c);
           }
-          acc_scale2(B, kc2, nc2, Z);
-          acc_add2(A, B.s, B.c);
+          acc_add2(B, Bz.s, Bz.c);
+          if (g.flags & PK_C2_MINUS1) {
+            acc_sub2(A, B);
+          } else {
+            if (g.flags & PK_C2_POW2) {
+              B.s = rmul2(B.s, kc2, Z);
+              B.c = rmul2(B.c, kc2, Z);
+            } else {
+              acc_scale2(B, kc2, nc2, Z);
+            }
+            acc_add2(A, B.s, B.c);
+          }
         }
         out[v] = acc_get2(A);
       }
@@ -383,7 +418,7 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
       if (PASS == 1) {
 #pragma unroll
         for (int v = 0; v < K::VP; ++v) {
-          const int cell = k0 + tx * K::VP + v;
+          const int cell = k0 + tx + v * K::TX;
           if (cell < g.nc) reinterpret_cast<ulonglong2 *>(yout)[obase + cell] = make_ulonglong2(out[v].h, out[v].l);
         }
       } else {
@@ -403,16 +438,17 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, 2)
           float ha, hb, la, lb;
           upk2(zh, ha, hb);
           upk2(zl, la, lb);
-          da[v] = f2d_bits(ha, ebias, g.sexp) + f2d_bits(la, ebias, g.sexp);
-          db[v] = f2d_bits(hb, ebias, g.sexp) + f2d_bits(lb, ebias, g.sexp);
+          da[v] = f2d_bits(ha, ebias, bad) + f2d_bits(la, ebias, bad);
+          db[v] = f2d_bits(hb, ebias, bad) + f2d_bits(lb, ebias, bad);
         }
         double *yo = static_cast<double *>(yout) + obase;
-        const int xa = k0 + tx * K::VP - g.off_out, xb = xa + g.nc;
+        const int xa = k0 + tx - g.off_out, xb = xa + g.nc;
 #pragma unroll
         for (int v = 0; v < K::VP; ++v) {
-          if (k0 + tx * K::VP + v >= g.nc) continue;
-          if (xa + v >= 0 && xa + v < g.nx) yo[xa + v] = da[v];
-          if (xb + v >= 0 && xb + v < g.nx) yo[xb + v] = db[v];
+          if (k0 + tx + v * K::TX >= g.nc) continue;
+          const int o = v * K::TX;
+          if (xa + o >= 0 && xa + o < g.nx) yo[xa + o] = da[v];
+          if (xb + o >= 0 && xb + o < g.nx) yo[xb + o] = db[v];
         }
       }
     }
@@ -491,6 +527,11 @@ static int launch_pk(const void *x, void *y, const int64_t *dims, int bc, const 
   g.c0 = c[0];
   g.c1 = c[1];
   g.c2 = c[2];
+  auto pow2 = [](float v) {  // +-2^k: products are exact
+    int e = 0;
+    return v != 0.0f && std::fabs(std::frexp(v, &e)) == 0.5f;
+  };
+  g.flags = (pow2(c[1]) ? PK_C1_POW2 : 0) | (pow2(c[2]) ? PK_C2_POW2 : 0) | (c[2] == -1.0f ? PK_C2_MINUS1 : 0);
   if (PASS == 2) {  // scale = m * 2^e, m in [1, 2), m as an exact pair of floats
     int e = 0;
     const double m = std::frexp(scale, &e) * 2.0;
