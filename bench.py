@@ -696,7 +696,7 @@ def main():
                 "hbm_frac_of_measured": dstat["gbs"] / hbm}
     else:
         kern = {"flat": "flat_apply_kernel", "nested": "flat_apply_kernel x2 (nested B(A x))",
-                "pair": "df_lap_kernel x2 (FP64 in FP32 pairs, nested B(A x))"}[dstat["how"]]
+                "pair": "pk_lap_kernel x2 (FP64 as packed f32x2 pairs, nested B(A x))"}[dstat["how"]]
         roof = {"bound": "hbm", "achieved": dstat["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": dstat["gbs"] / hbm, "traffic": traffic, "kernel": f"{kern} ({dname})",
                 "peak_source": f"{src} hbm_gbs"}
