@@ -184,18 +184,14 @@ struct PkPass {
   static constexpr int PYS = BY + 2 * RP;
   static constexpr int KS = D + 2 * HX;  // cells per smem row
   static constexpr int FPLANE = KS * PYS;
-  // pass 1 stages raw doubles: two segments (lanes a and b) per row, each
-  // D + 2 HX values plus one spare 16-byte chunk for an odd half-row offset
-  static constexpr int SEG = D + 2 * HX + 2;
-  static constexpr int RPLANE = PASS == 1 ? 2 * SEG * PYS : 0;
-  static constexpr int NRAW = PASS == 1 ? PF + 1 : 0;
-  static constexpr int NRAWM = NRAW > 0 ? NRAW : 1;  // ring index modulus
-  static constexpr int NF = PASS == 1 ? R + 1 : R + 1 + PF;  // folded planes in smem
-  static constexpr int NQ = 2 * R + 1;                      // register queue of centre cells
-  static constexpr int NCH = PASS == 1 ? PYS * SEG : FPLANE; // 16-byte copies per plane
-  static constexpr int NCPT = (NCH + NTHR - 1) / NTHR;
-  static constexpr int NFPT = (FPLANE + NTHR - 1) / NTHR;    // fold work per thread (pass 1)
-  static constexpr size_t SMEM = size_t(NRAW) * RPLANE * 8 + size_t(NF) * FPLANE * 16;
+  // folded planes in smem: R behind the consumed one, the consumed one, PF
+  // in flight.  Pass 1 copies each double (8 bytes) straight into its lane
+  // of the cell and the copying thread splits the cell in place; pass 2
+  // copies whole 16-byte cells.
+  static constexpr int NF = R + 1 + PF;
+  static constexpr int NQ = 2 * R + 1;                     // register queue of centre cells
+  static constexpr int NCPT = (FPLANE + NTHR - 1) / NTHR;  // cells copied per thread
+  static constexpr size_t SMEM = size_t(NF) * FPLANE * 16;
 };
 
 enum { PK_C1_POW2 = 1, PK_C2_POW2 = 2, PK_C2_MINUS1 = 4 };
@@ -220,8 +216,7 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2
     pk_lap_kernel(const void *__restrict__ xin, void *__restrict__ yout, PkGeom g, int *__restrict__ bad_flag) {
   using K = PkPass<NDIM, R, PASS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2 *fold = reinterpret_cast<ulonglong2 *>(smem_raw + size_t(K::NRAW) * K::RPLANE * 8);
-  const unsigned long long *raw = reinterpret_cast<const unsigned long long *>(smem_raw);
+  ulonglong2 *fold = reinterpret_cast<ulonglong2 *>(smem_raw);
   const int tid = threadIdx.x;
   const int tx = tid % K::TX, ty = tid / K::TX;
   const int k0 = blockIdx.x * K::D;  // first cell of the tile
@@ -233,26 +228,30 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2
   const long long in_ps = NDIM == 3 ? g.in_ss : g.in_sy;
   int bad = 0;
 
-  // In-plane source offsets of this thread's 16-byte copies (fixed for the
-  // CTA); -1: zero fill.  Pass 2 also notes the cells whose lanes are swapped.
-  int src_off[K::NCPT];
+  // In-plane source offsets of this thread's cells (fixed for the CTA);
+  // -1: zero fill.  Pass 1: one double per lane; pass 2: one 16-byte cell,
+  // noting the cells whose lanes are swapped.
+  constexpr int NSRC = PASS == 1 ? 2 : 1;
+  int src_off[K::NCPT][NSRC];
   unsigned swap_mask = 0;
-  const int ob = g.nc & 1;
 #pragma unroll
   for (int i = 0; i < K::NCPT; ++i) {
     const int ch = tid + i * K::NTHR;
-    src_off[i] = -1;
-    if (ch >= K::NCH) continue;
+#pragma unroll
+    for (int l = 0; l < NSRC; ++l) src_off[i][l] = -1;
+    if (ch >= K::FPLANE) continue;
+    const int r = ch / K::KS, c = ch - r * K::KS;
+    int iy = 0;
+    if (NDIM == 3) iy = map_coord(y0 - K::RP + r, g.ny, g.bc, R);
+    if (iy < 0) continue;
     if (PASS == 1) {
-      const int r = ch / K::SEG, rem = ch - r * K::SEG;  // SEG/2 chunks per segment row
-      const int gsel = rem / (K::SEG / 2), j = rem - gsel * (K::SEG / 2);
-      const int p = (gsel ? k0 + g.nc - K::HX - ob : k0 - K::HX) + 2 * j;
-      const int ix = map_coord(p, g.nf, g.bc, R);
-      int iy = 0;
-      if (NDIM == 3) iy = map_coord(y0 - K::RP + r, g.ny, g.bc, R);
-      if (ix >= 0 && iy >= 0) src_off[i] = int((long long)iy * g.in_sy + ix);
+      const int p = k0 - K::HX + c;  // fold position of lane a; lane b is nc further
+#pragma unroll
+      for (int l = 0; l < NSRC; ++l) {
+        const int ix = map_coord(p + l * g.nc, g.nf, g.bc, R);
+        if (ix >= 0) src_off[i][l] = int((long long)iy * g.in_sy + ix);
+      }
     } else {
-      const int r = ch / K::KS, c = ch - r * K::KS;
       int gc = k0 - K::HX + c;
       bool sw = false;
       if (gc < 0) {
@@ -262,10 +261,8 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2
         gc -= g.nc;
         sw = true;
       }
-      int iy = 0;
-      if (NDIM == 3) iy = map_coord(y0 - K::RP + r, g.ny, g.bc, R);
-      if (gc >= 0 && gc < g.nc && iy >= 0) {
-        src_off[i] = int((long long)iy * g.in_sy + gc);
+      if (gc >= 0 && gc < g.nc) {
+        src_off[i][0] = int((long long)iy * g.in_sy + gc);
         if (sw) swap_mask |= 1u << i;
       }
     }
@@ -277,16 +274,18 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2
 #pragma unroll
     for (int i = 0; i < K::NCPT; ++i) {
       const int ch = tid + i * K::NTHR;
-      if (ch >= K::NCH) continue;
-      const bool ok = iz >= 0 && src_off[i] >= 0;
-      if (PASS == 1) {
-        unsigned long long *dst = const_cast<unsigned long long *>(raw) + size_t(t % K::NRAWM) * K::RPLANE + 2 * ch;
-        const unsigned long long *src = static_cast<const unsigned long long *>(xin) + (ok ? pb + src_off[i] : 0);
-        cp_async16(dst, src, ok ? 16 : 0);
-      } else {
-        ulonglong2 *dst = fold + size_t(t % K::NF) * K::FPLANE + ch;
-        const ulonglong2 *src = static_cast<const ulonglong2 *>(xin) + (ok ? pb + src_off[i] : 0);
-        cp_async16(dst, src, ok ? 16 : 0);
+      if (ch >= K::FPLANE) continue;
+      ulonglong2 *dst = fold + size_t(t % K::NF) * K::FPLANE + ch;
+#pragma unroll
+      for (int l = 0; l < NSRC; ++l) {
+        const bool ok = iz >= 0 && src_off[i][l] >= 0;
+        if (PASS == 1) {
+          const unsigned long long *src = static_cast<const unsigned long long *>(xin) + (ok ? pb + src_off[i][l] : 0);
+          cp_async_elem<8>(reinterpret_cast<unsigned long long *>(dst) + l, src, ok ? 8 : 0);
+        } else {
+          const ulonglong2 *src = static_cast<const ulonglong2 *>(xin) + (ok ? pb + src_off[i][l] : 0);
+          cp_async16(dst, src, ok ? 16 : 0);
+        }
       }
     }
   };
@@ -314,7 +313,20 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2
       if (t >= NT) break;
       cp_async_wait<K::PF - 1>();
       ulonglong2 *fp = fold + size_t(t % K::NF) * K::FPLANE;
-      if (PASS == 2 && swap_mask) {  // own copies have landed: swap the wrapped cells' lanes
+      // own copies have landed: split pass 1's doubles into pairs in place,
+      // swap the lanes of pass 2's wrapped cells
+      if (PASS == 1) {
+#pragma unroll
+        for (int i = 0; i < K::NCPT; ++i) {
+          const int ch = tid + i * K::NTHR;
+          if (ch >= K::FPLANE) continue;
+          const ulonglong2 v = fp[ch];
+          float ha, la, hb, lb;
+          split_double(__longlong_as_double((long long)v.x), ha, la, bad);
+          split_double(__longlong_as_double((long long)v.y), hb, lb, bad);
+          fp[ch] = make_ulonglong2(pk2(ha, hb), pk2(la, lb));
+        }
+      } else if (swap_mask) {
 #pragma unroll
         for (int i = 0; i < K::NCPT; ++i)
           if (swap_mask & (1u << i)) {
@@ -330,22 +342,6 @@ __global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2
       __syncthreads();
       if (t + K::PF < NT) load_plane(t + K::PF);
       cp_async_commit();
-      if (PASS == 1) {  // split and fold the arrived doubles
-        const unsigned long long *rp = raw + size_t(t % K::NRAWM) * K::RPLANE;
-#pragma unroll
-        for (int i = 0; i < K::NFPT; ++i) {
-          const int f = tid + i * K::NTHR;
-          if (f >= K::FPLANE) continue;
-          const int r = f / K::KS, c = f - r * K::KS;
-          const double va = __longlong_as_double((long long)rp[(2 * r) * K::SEG + c]);
-          const double vb = __longlong_as_double((long long)rp[(2 * r + 1) * K::SEG + c + ob]);
-          float ha, la, hb, lb;
-          split_double(va, ha, la, bad);
-          split_double(vb, hb, lb, bad);
-          fp[f] = make_ulonglong2(pk2(ha, hb), pk2(la, lb));
-        }
-        __syncthreads();
-      }
       // centre cells of this plane into the queue
 #pragma unroll
       for (int v = 0; v < K::VP; ++v) {
