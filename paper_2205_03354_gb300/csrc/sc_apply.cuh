@@ -61,13 +61,16 @@ template <>
 struct TileCfg<double, 2, 0> {
   static constexpr int VX = 2, VY = 1, TX = 128, TY = 1;
 };
+// 2D solver tiles: TY warps stream TY independent row ranges of one
+// TX * VX wide column (see FlatApply::WS), so narrow grids keep every lane
+// busy and a small problem splits into many short tiles.
 template <>
 struct TileCfg<float, 2, 1> {
-  static constexpr int VX = 4, VY = 1, TX = 128, TY = 1;
+  static constexpr int VX = 2, VY = 1, TX = 32, TY = 4;
 };
 template <>
 struct TileCfg<double, 2, 1> {
-  static constexpr int VX = 2, VY = 1, TX = 128, TY = 1;
+  static constexpr int VX = 2, VY = 1, TX = 32, TY = 4;
 };
 template <int FAM>
 struct TileCfg<float, 3, FAM> {
@@ -106,9 +109,23 @@ struct FlatApply {
   // solver's short tiles (family 1) are L2-latency bound and keep more
   static constexpr int NSTAGE = FAM == 0 ? 3 : (NDIM == 2 ? 8 : 4);
   static constexpr int NS = 2 * R + 1;          // pending output planes
+  // Warp streams (2D solver family): warp w of the CTA streams output rows
+  // [z0 + w H, z0 + (w + 1) H) of the tile's column with its own ring,
+  // synchronising with __syncwarp; a tile spans TY * H rows.
+  static constexpr bool WS = NDIM == 2 && FAM == 1;
+  static constexpr int NSTREAM = WS ? TY : 1;
+  static constexpr int LANES = WS ? TX : NTHR;  // threads sharing one ring
   static constexpr int NCHUNK = PLANE / CH;
-  static constexpr int CPT = (NCHUNK + NTHR - 1) / NTHR;  // chunks per thread
-  static constexpr size_t SMEM = size_t(NSTAGE) * PLANE * sizeof(T);
+  static constexpr int CPT = (NCHUNK + LANES - 1) / LANES;  // chunks per thread
+  static constexpr size_t SMEM = size_t(NSTREAM) * NSTAGE * PLANE * sizeof(T);
+
+  static __device__ __forceinline__ int lid() { return WS ? int(threadIdx.x) % TX : int(threadIdx.x); }
+  static __device__ __forceinline__ void ring_sync() {
+    if (WS)
+      __syncwarp();
+    else
+      __syncthreads();
+  }
 
   static __device__ __forceinline__ int wsidx(int ds, int dp, int dx) {
     return NDIM == 3 ? ((ds + R) * (2 * R + 1) + (dp + R)) * (2 * R + 1) + (dx + R)
@@ -130,7 +147,7 @@ struct FlatApply {
     if (g.vec) {
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
-        const int c = threadIdx.x + k * NTHR;
+        const int c = lid() + k * LANES;
         if (c < NCHUNK) {
           const int o = coff[k];
           const bool ok = (iz >= 0) & (o >= 0);
@@ -139,7 +156,7 @@ struct FlatApply {
         }
       }
     } else {
-      for (int e = threadIdx.x; e < PLANE; e += NTHR) {
+      for (int e = lid(); e < PLANE; e += LANES) {
         const int r = e / PXS, cc = e - r * PXS;
         const int gx = x0 - HX + cc;
         int ix = map_coord(gx, g.nx, g.bc, R);
@@ -157,7 +174,7 @@ struct FlatApply {
                                                        int *coff) {
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
-      const int c = threadIdx.x + k * NTHR;
+      const int c = lid() + k * LANES;
       int o = -1;
       if (c < NCHUNK) {
         const int e = c * CH;
@@ -178,10 +195,15 @@ struct FlatApply {
   static __device__ __forceinline__ void run_tile(const T *__restrict__ x, const ApplyGeom &g,
                                                   const WT &W, int x0, int y0, int z0, T *smem,
                                                   EPI &epi) {
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    if (WS) {  // this warp's row range and ring
+      z0 += ty * g.H;
+      smem += size_t(ty) * NSTAGE * PLANE;
+      ty = 0;
+    }
     const int ns = NDIM == 3 ? g.nz : g.ny;
     const int zend = min(z0 + g.H, ns);
-    const int NT = (zend - z0) + 2 * R;
+    const int NT = zend > z0 ? (zend - z0) + 2 * R : 0;
     int coff[CPT];
     if (g.vec) chunk_offsets(g, x0, y0, coff);
 
@@ -206,7 +228,7 @@ struct FlatApply {
         const int t = tb + s;
         if (t >= NT) break;
         cp_async_wait<NSTAGE - 2>();
-        __syncthreads();
+        ring_sync();
         {
           const int tl = t + NSTAGE - 1;
           if (tl < NT) load_plane(x, g, x0, y0, z0 - R + tl, smem + (tl % NSTAGE) * PLANE, coff);

@@ -218,15 +218,20 @@ static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
   const long long txy = ((nx + K::BX - 1) / K::BX) * (NDIM == 3 ? (ny + K::BY - 1) / K::BY : 1);
   const long long planes = NDIM == 3 ? nz : ny;
   const long long npts = nx * ny * nz;
-  // about one tile per 2048 points, at most ~1024 tiles
-  const long long target = std::max<long long>(1, std::min<long long>(npts / 2048, 1024));
-  long long h = (txy * planes + target - 1) / target;
-  // at least 8 rows (2D) / 4 planes (3D) per tile: the 2R halo rows are
-  // re-read by the neighbouring tile
-  h = std::max<long long>(NDIM == 2 ? 8 : 4, std::min<long long>(h, 128));
-  h = std::min<long long>(h, planes);
+  const long long ns = K::NSTREAM;  // 2D: row streams per tile, h rows each
+  // 3D: about one tile per 2048 points, at most ~1024 tiles.  2D: one per
+  // 1024 points (short row streams keep small grids parallel), at most one
+  // round of the CTAs a 2D launch keeps resident (4 per SM)
+  const long long target =
+      NDIM == 3 ? std::max<long long>(1, std::min<long long>(npts / 2048, 1024))
+                : std::max<long long>(1, std::min<long long>(npts / 1024, 4LL * num_sms()));
+  long long h = (txy * planes + target * ns - 1) / (target * ns);
+  // at least 2 rows per 2D stream / 4 planes per 3D tile (the 2R halo is
+  // re-read by the neighbouring stream or tile), at most 128
+  h = std::max<long long>(NDIM == 2 ? 2 : 4, std::min<long long>(h, 128));
+  h = std::min<long long>(h, (planes + ns - 1) / ns);
   H = int(h);
-  ntiles = int(txy * ((planes + h - 1) / h));
+  ntiles = int(txy * ((planes + h * ns - 1) / (h * ns)));
 }
 
 static size_t smem_bytes_cg() {

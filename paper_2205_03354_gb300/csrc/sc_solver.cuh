@@ -262,7 +262,7 @@ __device__ __forceinline__ void tile_origin(const SolveProb &P, int tile, int H,
   } else {
     x0 = (tile % tx) * K::BX;
     y0 = 0;
-    z0 = (tile / tx) * H;
+    z0 = (tile / tx) * H * K::NSTREAM;
   }
 }
 
