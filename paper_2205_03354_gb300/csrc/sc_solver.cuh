@@ -72,6 +72,9 @@ constexpr int CG_NTHR = 128;
 constexpr int CG_STEP = CG_NTHR * 4;      // elements per vector-phase step (4 per thread)
 constexpr int CG_CHUNK = CG_STEP * 8;     // largest chunk used for sizing scratch (see P.chunk)
 constexpr long long SPIN_LIMIT = 1LL << 24;  // ~1-2 s with the back-off below
+// group reductions whose CTAs x partials x values stay below this read all
+// partials in every CTA instead of waiting for a published result
+constexpr long long ALLREAD_MAX = 16384;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   unsigned v;
@@ -130,6 +133,39 @@ __device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *ou
       if (threadIdx.x == 0) s_out[k] = v;
     }
     if (deadline && threadIdx.x == 0) s_out[3] = global_ns() >= deadline ? 1.0 : 0.0;
+    __syncthreads();
+  } else if (deadline == 0ull && (long long)P.ncta * nused * nval <= ALLREAD_MAX) {
+    // small group: every CTA waits for the arrival count alone and then sums
+    // the partials itself in the same fixed order (the same bits in every
+    // CTA), one publish round trip shorter than the path below
+    G.target += P.ncta;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&P.bar[0], 1u);
+      long long spins = 0;
+      *G.flag = 0;
+      while (ld_acquire(&P.bar[0]) < G.target) {
+        if (++spins > G.spin_limit) {
+          *G.flag = -1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __syncthreads();
+    if (*G.flag == -1) {
+      ok = false;
+      if (threadIdx.x == 0) {
+        P.st->status = SC_ETIMEOUT;
+        P.st->phase = 2;
+      }
+    } else {
+      __threadfence();
+      for (int k = 0; k < nval; ++k) {
+        const double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
+        if (threadIdx.x == 0) s_out[k] = v;
+      }
+    }
     __syncthreads();
   } else {
     G.target += P.ncta;
