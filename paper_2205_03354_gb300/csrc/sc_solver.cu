@@ -221,10 +221,12 @@ static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
   const long long ns = K::NSTREAM;  // 2D: row streams per tile, h rows each
   // 3D: about one tile per 2048 points, at most ~1024 tiles.  2D: one per
   // 1024 points (short row streams keep small grids parallel), at most one
-  // round of the CTAs a 2D launch keeps resident (4 per SM)
+  // round of the CTAs a 2D launch keeps resident (4 per SM).  FP64 tiles
+  // are 4x smaller: a warp retires one FP64 FMA instruction per 64 clocks
+  const long long per = (NDIM == 3 ? 2048 : 1024) / (sizeof(T) == 8 ? 4 : 1);
   const long long target =
-      NDIM == 3 ? std::max<long long>(1, std::min<long long>(npts / 2048, 1024))
-                : std::max<long long>(1, std::min<long long>(npts / 1024, 4LL * num_sms()));
+      NDIM == 3 ? std::max<long long>(1, std::min<long long>(npts / per, 1024))
+                : std::max<long long>(1, std::min<long long>(npts / per, 4LL * num_sms()));
   long long h = (txy * planes + target * ns - 1) / (target * ns);
   // at least 2 rows per 2D stream / 4 planes per 3D tile (the 2R halo is
   // re-read by the neighbouring stream or tile), at most 128
