@@ -231,7 +231,9 @@ struct CgApplyEpi {
   T *__restrict__ q;
   long long sy, ss;
   int nx;
-  double a, b, dot;
+  T a, b;
+  T dot;  // this thread's partial p.q, accumulated in the inner type (FP32
+          // inner iterations accumulate in FP32; the group sum is FP64)
   __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX]) {
     const long long base = (long long)j * (NDIM == 3 ? ss : sy) + (NDIM == 3 ? (long long)yy * sy : 0);
 #pragma unroll
@@ -239,9 +241,9 @@ struct CgApplyEpi {
       if (xo + vx < nx) {
         const long long i = base + xo + vx;
         const T pv = __ldcg(p + i);
-        const T qv = T(a) * pv + T(b) * v[vx];
+        const T qv = a * pv + b * v[vx];
         q[i] = qv;
-        dot += double(pv) * double(qv);
+        dot = fma(pv, qv, dot);
       }
     }
   }
@@ -320,9 +322,9 @@ __device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, d
     int x0, y0, z0;
     tile_origin<K>(P, tile, P.H_in, NDIM, x0, y0, z0);
     CgApplyEpi<T, NDIM, K::VX> epi{static_cast<const T *>(P.p), static_cast<T *>(P.q), g.out_sy,
-                                   g.out_ss, P.nx, P.a, P.b, 0.0};
+                                   g.out_ss, P.nx, T(P.a), T(P.b), T(0)};
     K::run_tile(static_cast<const T *>(P.p), g, W, x0, y0, z0, reinterpret_cast<T *>(smem), epi);
-    const double s = block_sum<CG_NTHR>(epi.dot, red);
+    const double s = block_sum<CG_NTHR>(double(epi.dot), red);
     if (threadIdx.x == 0) P.part[tile] = s;
   }
 }
@@ -400,7 +402,7 @@ __device__ __forceinline__ void vec_elems(const SolveProb &P, long long i, int n
       d[i] = __ldcg(d + i) + al * pv;
       const TI v = __ldcg(rh + i) - al * __ldcg(q + i);
       rh[i] = v;
-      a0 += double(v) * double(v);
+      a0 += double(v * v);
     } else if (KIND == 2) {
       p[i] = __ldcg(rh + i) + TI(s1) * __ldcg(p + i);
     } else if (KIND == 3) {
@@ -426,6 +428,7 @@ __device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) 
     const long long e0 = (long long)c * P.chunk;
     const long long e1 = min(e0 + P.chunk, P.npts);
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    TI acc_t = TI(0);  // the update's partial rh.rh in the inner type (FP32 accumulation)
     if (P.vec_v && e1 - e0 == P.chunk) {
       const int nsteps = P.chunk / CG_STEP;
 #pragma unroll 4
@@ -457,7 +460,7 @@ __device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) 
           for (int j = 0; j < 4; ++j) {
             dv[j] = dv[j] + al * pv[j];
             rv[j] = rv[j] - al * qv[j];
-            a0 += double(rv[j]) * double(rv[j]);
+            acc_t = fma(rv[j], rv[j], acc_t);
           }
           st4(d + i, dv);
           st4(rh + i, rv);
@@ -505,7 +508,7 @@ __device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) 
         vec_elems<TI, KIND>(P, i, int(min(4LL, e1 - i)), s1, a0, a1, a2);
     }
     if (KIND == 0 || KIND == 1 || KIND == 4 || KIND == 5) {
-      const double t0 = block_sum<CG_NTHR>(a0, red);
+      const double t0 = block_sum<CG_NTHR>(a0 + double(acc_t), red);
       if (threadIdx.x == 0) P.part[c] = t0;
       if (KIND == 0) {
         const double t1 = block_sum<CG_NTHR>(a1, red);
