@@ -429,7 +429,51 @@ __device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) 
     const long long e1 = min(e0 + P.chunk, P.npts);
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     TI acc_t = TI(0);  // the update's partial rh.rh in the inner type (FP32 accumulation)
-    if (P.vec_v && e1 - e0 == P.chunk) {
+    if ((KIND == 1 || KIND == 2) && P.vec_v && e1 - e0 == P.chunk && P.chunk >= 2 * CG_STEP) {
+      // the per-iteration updates: two steps' loads issued before any store
+      // (the vectors may alias as far as the compiler knows, so it would not
+      // hoist them itself); chunks are CG_STEP * 2^k
+      const int nsteps = P.chunk / CG_STEP;
+      for (int k = 0; k < nsteps; k += 2) {
+        const long long i0 = e0 + 4LL * (k * CG_NTHR + threadIdx.x), i1 = i0 + 4LL * CG_NTHR;
+        if (KIND == 1) {
+          TI pv[2][4], dv[2][4], rv[2][4], qv[2][4];
+          ld4(p + i0, pv[0]);
+          ld4(p + i1, pv[1]);
+          ld4(d + i0, dv[0]);
+          ld4(d + i1, dv[1]);
+          ld4(rh + i0, rv[0]);
+          ld4(rh + i1, rv[1]);
+          ld4(q + i0, qv[0]);
+          ld4(q + i1, qv[1]);
+          const TI al = TI(s1);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              dv[h][j] = dv[h][j] + al * pv[h][j];
+              rv[h][j] = rv[h][j] - al * qv[h][j];
+              acc_t = fma(rv[h][j], rv[h][j], acc_t);
+            }
+          st4(d + i0, dv[0]);
+          st4(d + i1, dv[1]);
+          st4(rh + i0, rv[0]);
+          st4(rh + i1, rv[1]);
+        } else {
+          TI pv[2][4], rv[2][4];
+          ld4(p + i0, pv[0]);
+          ld4(p + i1, pv[1]);
+          ld4(rh + i0, rv[0]);
+          ld4(rh + i1, rv[1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pv[h][j] = rv[h][j] + TI(s1) * pv[h][j];
+          st4(p + i0, pv[0]);
+          st4(p + i1, pv[1]);
+        }
+      }
+    } else if (P.vec_v && e1 - e0 == P.chunk) {
       const int nsteps = P.chunk / CG_STEP;
 #pragma unroll 4
       for (int k = 0; k < nsteps; ++k) {
