@@ -107,7 +107,13 @@ struct FlatApply {
   static constexpr int PLANE = PXS * PYS;
   // planes in the ring: streaming applies (family 0) keep 2 in flight; the
   // solver's short tiles (family 1) are L2-latency bound and keep more
-  static constexpr int NSTAGE = FAM == 0 ? 3 : (NDIM == 2 ? 8 : 4);
+  static constexpr int NSTAGE = FAM == 0 ? 3 : (NDIM == 2 ? 8 : 6);
+  // the solver family keeps the R input planes behind the consumed one in the
+  // ring, so that an epilogue reads each output's own input value from shared
+  // memory; loads run NSTAGE - 1 - KEEP planes ahead
+  static constexpr int KEEP = FAM == 1 ? R : 0;
+  static constexpr int PD = NSTAGE - 1 - KEEP;
+  static_assert(PD >= 1, "ring too short for the kept planes");
   static constexpr int NS = 2 * R + 1;          // pending output planes
   // Warp streams (2D solver family): warp w of the CTA streams output rows
   // [z0 + w H, z0 + (w + 1) H) of the tile's column with its own ring,
@@ -216,7 +222,7 @@ struct FlatApply {
         for (int b = 0; b < VX; ++b) acc[s][a][b] = T(0);
 
 #pragma unroll
-    for (int k = 0; k < NSTAGE - 1; ++k) {
+    for (int k = 0; k < PD; ++k) {
       if (k < NT) load_plane(x, g, x0, y0, z0 - R + k, smem + k * PLANE, coff);
       cp_async_commit();
     }
@@ -227,10 +233,10 @@ struct FlatApply {
       for (int s = 0; s < NS; ++s) {
         const int t = tb + s;
         if (t >= NT) break;
-        cp_async_wait<NSTAGE - 2>();
+        cp_async_wait<PD - 1>();
         ring_sync();
         {
-          const int tl = t + NSTAGE - 1;
+          const int tl = t + PD;
           if (tl < NT) load_plane(x, g, x0, y0, z0 - R + tl, smem + (tl % NSTAGE) * PLANE, coff);
           cp_async_commit();
         }
@@ -265,11 +271,14 @@ struct FlatApply {
           const int sc_ = ((s - 2 * R) % NS + NS) % NS;
           const int j = z0 + t - 2 * R;
           if (t >= 2 * R && j < zend) {
+            // input plane j (consumed R steps ago) is still in the ring when KEEP
+            const T *pj = smem + ((t - R) % NSTAGE) * PLANE;
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy) {
               const int yy = NDIM == 3 ? y0 + ty * VY + vy : 0;
               if (NDIM == 3 && yy >= g.ny) continue;
-              epi(j, yy, xo, acc[sc_][vy]);
+              const T *ctr = KEEP ? pj + (ty * VY + vy + RP) * PXS + tx * VX + HX : nullptr;
+              epi(j, yy, xo, acc[sc_][vy], ctr);
             }
           }
 #pragma unroll
@@ -289,7 +298,7 @@ template <typename T, int NDIM, int VX>
 struct StoreEpi {
   T *__restrict__ y;
   const ApplyGeom *g;
-  __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX]) const {
+  __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX], const T *) const {
     T *dst = y + (long long)j * (NDIM == 3 ? g->out_ss : g->out_sy) +
              (NDIM == 3 ? (long long)yy * g->out_sy : 0) + xo;
     if (g->vec && xo + VX <= g->nx && (sizeof(T) * VX) % 16 == 0) {

@@ -234,13 +234,14 @@ struct CgApplyEpi {
   T a, b;
   T dot;  // this thread's partial p.q, accumulated in the inner type (FP32
           // inner iterations accumulate in FP32; the group sum is FP64)
-  __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX]) {
+  // ctr: p at the VX outputs, from the tile's shared-memory ring
+  __device__ __forceinline__ void operator()(int j, int yy, int xo, const T (&v)[VX], const T *ctr) {
     const long long base = (long long)j * (NDIM == 3 ? ss : sy) + (NDIM == 3 ? (long long)yy * sy : 0);
 #pragma unroll
     for (int vx = 0; vx < VX; ++vx) {
       if (xo + vx < nx) {
         const long long i = base + xo + vx;
-        const T pv = __ldcg(p + i);
+        const T pv = ctr[vx];
         const T qv = a * pv + b * v[vx];
         q[i] = qv;
         dot = fma(pv, qv, dot);
@@ -258,13 +259,14 @@ struct ResidEpi {
   long long sy, ss;
   int nx;
   double a, b, dot;
-  __device__ __forceinline__ void operator()(int j, int yy, int xo, const double (&v)[VX]) {
+  // ctr: x at the VX outputs, from the tile's shared-memory ring
+  __device__ __forceinline__ void operator()(int j, int yy, int xo, const double (&v)[VX], const double *ctr) {
     const long long base = (long long)j * (NDIM == 3 ? ss : sy) + (NDIM == 3 ? (long long)yy * sy : 0);
 #pragma unroll
     for (int vx = 0; vx < VX; ++vx) {
       if (xo + vx < nx) {
         const long long i = base + xo + vx;
-        const double rv = __ldcg(rhs + i) - fma(b, v[vx], a * __ldcg(x + i));
+        const double rv = __ldcg(rhs + i) - fma(b, v[vx], a * ctr[vx]);
         r[i] = rv;
         dot += rv * rv;
       }
