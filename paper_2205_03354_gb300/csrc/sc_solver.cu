@@ -12,6 +12,7 @@
 
 #include "sc_apply_host.h"
 #include "sc_internal.h"
+#include "sc_cg_kernels.h"
 #include "sc_solver.cuh"
 #include "sc_solver_host.h"
 #include "sc_stats_kernels.h"
@@ -21,50 +22,6 @@ namespace sc {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-
-// DIMS: 1 = 2D problems only, 2 = 3D only, 3 = both (a kernel holding only
-// the tile routines it needs uses fewer registers, so more CTAs fit).
-// TI = void: both precision classes in one launch, chosen per problem.
-template <typename TI, int R, int DIMS>
-__global__ void __launch_bounds__(CG_NTHR, DIMS == 3 ? 3 : 4)
-    cg_persistent_kernel(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob,
-                         long long budget, unsigned long long slice_ns) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[CG_NTHR / 32];
-  __shared__ int flag;
-  const int pi = cta_prob[blockIdx.x];
-  if (pi < 0) return;
-  const SolveProb &P = probs[pi];
-  if (P.st->phase == 2) return;
-  GroupCtx G{&P, int(blockIdx.x) - P.cta0, 0u, 0u, red, &flag};
-  if (DIMS & 1) {
-    if (P.ndim == 2) cg_run<TI, 2, R>(G, smem, budget, slice_ns);
-  }
-  if (DIMS & 2) {
-    if (P.ndim == 3) cg_run<TI, 3, R>(G, smem, budget, slice_ns);
-  }
-}
-
-template <int R, int DIMS>
-__global__ void __launch_bounds__(CG_NTHR, 3)
-    cg_persistent_both(const SolveProb *__restrict__ probs, const int *__restrict__ cta_prob, long long budget,
-                       unsigned long long slice_ns) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[CG_NTHR / 32];
-  __shared__ int flag;
-  const int pi = cta_prob[blockIdx.x];
-  if (pi < 0) return;
-  const SolveProb &P = probs[pi];
-  if (P.st->phase == 2) return;
-  GroupCtx G{&P, int(blockIdx.x) - P.cta0, 0u, 0u, red, &flag};
-  if (P.mixed) {
-    if ((DIMS & 1) && P.ndim == 2) cg_run<float, 2, R>(G, smem, budget, slice_ns);
-    if ((DIMS & 2) && P.ndim == 3) cg_run<float, 3, R>(G, smem, budget, slice_ns);
-  } else {
-    if ((DIMS & 1) && P.ndim == 2) cg_run<double, 2, R>(G, smem, budget, slice_ns);
-    if ((DIMS & 2) && P.ndim == 3) cg_run<double, 3, R>(G, smem, budget, slice_ns);
-  }
-}
 
 // out = ring of g (padded array), interior set to zero.
 __global__ void k_ring_copy(const double *__restrict__ g, double *__restrict__ out, int ndim,
@@ -411,16 +368,21 @@ static int assign_groups(std::vector<SolveProb> &hp, const std::vector<int> &idx
   return SC_OK;
 }
 
-typedef void (*CgKernel)(const SolveProb *, const int *, long long, unsigned long long);
-
+// the persistent kernel variants live in sc_cg_f32.cu, sc_cg_f64.cu and
+// sc_cg_both.cu (separate translation units, compiled in parallel)
 template <typename TI>
-static CgKernel cg_kernel_for(int dims) {
-  return dims == 1 ? cg_persistent_kernel<TI, 2, 1> : dims == 2 ? cg_persistent_kernel<TI, 2, 2>
-                                                               : cg_persistent_kernel<TI, 2, 3>;
+static CgKernel cg_kernel_for(int dims);
+template <>
+CgKernel cg_kernel_for<float>(int dims) {
+  return cg_kernel_f32(dims);
+}
+template <>
+CgKernel cg_kernel_for<double>(int dims) {
+  return cg_kernel_f64(dims);
 }
 template <>
 CgKernel cg_kernel_for<void>(int dims) {
-  return dims == 1 ? cg_persistent_both<2, 1> : dims == 2 ? cg_persistent_both<2, 2> : cg_persistent_both<2, 3>;
+  return cg_kernel_both(dims);
 }
 
 // Which dimensionalities occur among hp[idx] (bit 0: 2D, bit 1: 3D).

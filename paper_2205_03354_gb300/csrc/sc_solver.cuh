@@ -24,6 +24,7 @@
 // residual (the search direction is kept).  Convergence is only declared on
 // the FP64 true residual.
 #pragma once
+#include "../../include/stencilcomp.h"
 #include "sc_apply.cuh"
 
 namespace sc {
