@@ -333,3 +333,29 @@ def test_saved_tuning_runs_the_recorded_schedule(how, planes):
         sc.apply_composition(L, L, x, y2, work, h=(1, n), arith="pair" if how == "pair" else "native")
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("ndim,dims,bc", [(2, (256, 96), "periodic"), (3, (48, 40, 36), "periodic"),
+                                          (3, (40, 24, 20), "ghosted"), (2, (130, 70), "zero")])
+def test_pair_arithmetic_wide_dynamic_range(ndim, dims, bc):
+    """Fields whose magnitudes span 2^-60 .. 2^90 (inside the pair path's
+    window), with exact zeros and a constant patch: the split into FP32
+    pairs, the error-free sums and the exact rebuild keep every output
+    within 2^-42 of (|B| o |A|)|x|, and the pair passes (not the native
+    fallback) produced it."""
+    L = sc.laplacian(ndim, 4)
+    oL = ost.laplacian(ndim, 4)
+    R = 2 * oL.radius
+    n = dims[0]
+    shape = tuple(reversed(dims))
+    xshape = tuple(s + 2 * R for s in shape) if bc == "ghosted" else shape
+    x = fields.wide_range(xshape, seed=zlib.crc32(repr(("wide", ndim, dims, bc)).encode()), lo_exp=-60,
+                          hi_exp=90, zero_frac=0.05, patch=8)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.full(shape, float("nan"), dtype=torch.float64, device=DEV)
+    yn = torch.full(shape, float("nan"), dtype=torch.float64, device=DEV)
+    sc.apply_composition(L, L, xt, yt, bc=bc, h=(1, n), dims=dims, arith="pair")
+    sc.apply_composition(L, L, xt, yn, bc=bc, h=(1, n), dims=dims, arith="native")
+    torch.cuda.synchronize()
+    _nested_check(L, oL, x, yt, bc, n, 2.0 ** -42)
+    assert not torch.equal(yt, yn)
