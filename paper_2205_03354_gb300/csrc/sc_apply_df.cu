@@ -165,7 +165,7 @@ template <int NDIM>
 struct PkCfg;
 template <>
 struct PkCfg<2> {
-  static constexpr int TX = 256, TY = 1, VP = 2, PF = 4;
+  static constexpr int TX = 128, TY = 1, VP = 2, PF = 2;
 };
 template <>
 struct PkCfg<3> {
@@ -212,7 +212,7 @@ struct PkGeom {
 };
 
 template <int NDIM, int R, int PASS>
-__global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 2)
+__global__ void __launch_bounds__(PkPass<NDIM, R, PASS>::NTHR, NDIM == 3 ? 3 : 4)
     pk_lap_kernel(const void *__restrict__ xin, void *__restrict__ yout, PkGeom g, int *__restrict__ bad_flag) {
   using K = PkPass<NDIM, R, PASS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
