@@ -113,11 +113,8 @@ static int launch_flat(const ApplyReq &q, const T *wts_sparse, cudaStream_t st) 
   const long long tiles = (long long)((g.nx + K::BX - 1) / K::BX) *
                           (NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : 1);
   auto kern = flat_apply_kernel<T, NDIM, R, CLS>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> smem_set{0};
+  set_smem_limit_once(kern, K::SMEM, smem_set);
   g.H = choose_h(kern, K::NTHR, K::SMEM, tiles, ns, R, q.planes > 0 ? q.planes : g_h_override);
   const uintptr_t xa = reinterpret_cast<uintptr_t>(q.x), ya = reinterpret_cast<uintptr_t>(q.y);
   bool vec = (xa % 16 == 0) && (ya % 16 == 0) && (g.nx % K::CH == 0);

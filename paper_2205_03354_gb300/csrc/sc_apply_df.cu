@@ -539,11 +539,8 @@ static int launch_pk(const void *x, void *y, const int64_t *dims, int bc, const 
   const int gx = (g.nc + K::D - 1) / K::D;
   const long long txy = (long long)gx * (NDIM == 3 ? (g.ny + K::BY - 1) / K::BY : 1);
   auto kern = pk_lap_kernel<NDIM, R, PASS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> smem_set{0};
+  set_smem_limit_once(kern, K::SMEM, smem_set);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, K::NTHR, K::SMEM);
   g.H = planes > 0 ? std::min(planes, ns)

@@ -1,6 +1,9 @@
 // Internal helpers shared by the library's translation units (not part of the
 // public ABI).
 #pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -8,6 +11,20 @@
 #include "../../include/stencilcomp.h"
 
 namespace sc {
+
+// Raises a kernel's dynamic shared-memory limit once per device (the
+// attribute is per device; concurrent callers may both set it, which is
+// harmless).  `done` holds one bit per device ordinal.
+template <typename K>
+inline void set_smem_limit_once(K *kern, size_t bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load(std::memory_order_acquire) & bit)) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    done.fetch_or(bit, std::memory_order_acq_rel);
+  }
+}
 
 // Records a reason for the calling thread and returns the status unchanged.
 int fail(int status, const char *fmt, ...);

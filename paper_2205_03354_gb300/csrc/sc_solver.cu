@@ -395,11 +395,8 @@ static int dims_mask(const std::vector<SolveProb> &hp, const std::vector<int> &i
 template <typename TI>
 static size_t cg_smem_setup(int dims) {
   const size_t smem = smem_bytes_cg();
-  static bool attr[4] = {false, false, false, false};
-  if (!attr[dims]) {
-    cudaFuncSetAttribute(cg_kernel_for<TI>(dims), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr[dims] = true;
-  }
+  static std::atomic<unsigned long long> smem_set[4];
+  set_smem_limit_once(cg_kernel_for<TI>(dims), smem, smem_set[dims]);
   return smem;
 }
 
