@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -28,15 +29,19 @@ __global__ void __launch_bounds__(FlatApply<T, NDIM, R, CLS>::NTHR)
   K::run_tile(x, g, W, x0, y0, z0, smem, epi);
 }
 
-static int g_num_sms = 0;
+// SM count of the current device, cached per device ordinal (0: not read yet)
 int num_sms() {
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 152;
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int> &c = cache[dev & 63];
+  int n = c.load(std::memory_order_relaxed);
+  if (n <= 0) {
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+    c.store(n, std::memory_order_relaxed);
   }
-  return g_num_sms;
+  return n;
 }
 
 int wave_planes(long long tiles_xy, int nplanes, int R, long long slots, int hmin) {
@@ -80,7 +85,6 @@ static int choose_h(KERN kern, int nthr, size_t smem, long long tiles_per_plane,
   return wave_planes(tiles_per_plane, nplanes, R, slots, std::max(4 * R, 8));
 }
 
-static int g_h_override = 0;
 
 template <typename T, int NDIM, int R, int CLS>
 static int launch_flat(const ApplyReq &q, const T *wts_sparse, cudaStream_t st) {
@@ -115,7 +119,7 @@ static int launch_flat(const ApplyReq &q, const T *wts_sparse, cudaStream_t st) 
   auto kern = flat_apply_kernel<T, NDIM, R, CLS>;
   static std::atomic<unsigned long long> smem_set{0};
   set_smem_limit_once(kern, K::SMEM, smem_set);
-  g.H = choose_h(kern, K::NTHR, K::SMEM, tiles, ns, R, q.planes > 0 ? q.planes : g_h_override);
+  g.H = choose_h(kern, K::NTHR, K::SMEM, tiles, ns, R, q.planes);
   const uintptr_t xa = reinterpret_cast<uintptr_t>(q.x), ya = reinterpret_cast<uintptr_t>(q.y);
   bool vec = (xa % 16 == 0) && (ya % 16 == 0) && (g.nx % K::CH == 0);
   if (q.bc == SC_BC_GHOSTED) vec = vec && (q.s->radius == R) && ((R - K::HX) % K::CH == 0) &&
@@ -202,7 +206,6 @@ size_t grid_elems(const sc_stencil *s, int bc, const int64_t *dims, bool input) 
   return n;
 }
 
-void set_apply_planes_override(int h) { g_h_override = h; }
 
 // xp = x surrounded by a zero ring of width R (all dims).
 template <typename T>

@@ -38,6 +38,5 @@ int num_sms();
 // stream as long a run as the wave count allows.
 int wave_planes(long long tiles_xy, int nplanes, int R, long long slots, int hmin);
 // Testing/tuning knob: fixes the number of output planes per CTA (0 = auto).
-void set_apply_planes_override(int h);
 
 }  // namespace sc
