@@ -355,9 +355,11 @@ int sc_ch_stats_noalloc(const sc_ch *p, const double *u_dev, double *mass_host, 
 
 /* Failure-detection self-test of the solver's bounded group barrier: runs
  * the barrier for a group of two CTAs with only one launched, so the release
- * never comes; the wait gives up after spin_limit polls (1..2^24, ~100 ns
- * each) and *status_out receives SC_ETIMEOUT.  Nothing traps or faults; the
- * context stays usable.  work_bytes >= 4096. */
+ * never comes, once with each reduction protocol (every CTA reading the
+ * partials; the last arriver publishing the result); each wait gives up after
+ * spin_limit polls (1..2^24, ~100 ns each) and *status_out receives
+ * SC_ETIMEOUT when both did.  Nothing traps or faults; the context stays
+ * usable.  work_bytes >= 4096. */
 int sc_selftest_barrier_timeout(void *work_dev, size_t work_bytes, int64_t spin_limit, int32_t *status_out,
                                 sc_stream_t stream);
 

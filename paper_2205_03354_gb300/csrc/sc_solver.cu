@@ -819,13 +819,18 @@ __global__ void k_record_states(const SolveProb *__restrict__ probs, int n, Solv
 
 // A group of two CTAs of which only one is launched: its barrier can never
 // be released, so the bounded wait must run out and report SC_ETIMEOUT.
+// Both group-reduction protocols in turn (the small-group one, then the
+// publishing one, selected by a far-off deadline); the status is
+// SC_ETIMEOUT only if each gave up after its spin limit.
 __global__ void k_barrier_timeout_probe(SolveProb *P, long long spin_limit) {
   __shared__ double red[CG_NTHR / 32];
   __shared__ int flag;
   GroupCtx G{P, 0, 0u, 0u, red, &flag, spin_limit};
   double out[4];
   if (threadIdx.x == 0) P->part[0] = 1.0;
-  group_reduce(G, 1, 1, out);
+  const bool ok_small = group_reduce(G, 1, 1, out);
+  const bool ok_publish = group_reduce(G, 1, 1, out, ~0ull);
+  if (threadIdx.x == 0) P->st->status = (!ok_small && !ok_publish) ? SC_ETIMEOUT : SC_OK;
 }
 
 }  // namespace sc
