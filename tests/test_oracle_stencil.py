@@ -239,3 +239,33 @@ def test_weight_rounding_is_correct():
     mid2 = (Fraction(float(b)) + Fraction(float(c))) / 2
     assert st.round_f32(mid2) == c
     assert st.round_f64(Fraction(1, 3)) == 1.0 / 3.0
+
+
+def _random_stencil(rng, ndim, radius, npts):
+    coeffs = {}
+    while len(coeffs) < npts:
+        off = tuple(int(v) for v in rng.integers(-radius, radius + 1, size=ndim))
+        coeffs[off] = Fraction(int(rng.integers(-9, 10)) or 1, int(rng.integers(1, 7)))
+    return st.Stencil.make(coeffs, int(rng.integers(0, 3)))
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_taylor_coefficients_of_a_composition_are_the_cauchy_product(ndim):
+    """For C = A o B (Eq. C=B(A): offsets add, weights multiply) the binomial
+    theorem gives t^C_alpha = sum_{beta <= alpha} t^A_beta t^B_(alpha - beta):
+    the Taylor coefficients of a composition are the Cauchy product of the
+    factors'.  Random rational stencils with arbitrary offsets; exact
+    arithmetic.  A slip in the composition (an offset or weight mix-up) or
+    in the Taylor coefficients (a factorial or power) breaks the identity."""
+    rng = np.random.default_rng(20 + ndim)
+    for _ in range(6):
+        A = _random_stencil(rng, ndim, 3, 5)
+        B = _random_stencil(rng, ndim, 2, 4)
+        C = st.compose(A, B)
+        assert C.hpow == A.hpow + B.hpow
+        for alpha in itertools.product(range(4), repeat=ndim):
+            want = Fraction(0)
+            for beta in itertools.product(*(range(a + 1) for a in alpha)):
+                gamma = tuple(a - b for a, b in zip(alpha, beta))
+                want += st.taylor_coeff(A, beta) * st.taylor_coeff(B, gamma)
+            assert st.taylor_coeff(C, alpha) == want, (alpha, A, B)
