@@ -1,6 +1,7 @@
 """The C-ABI library without a GPU: it loads, exports every function the
 headers declare, and its exact host algebra matches the oracle bit for bit."""
 import ctypes
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -106,3 +107,47 @@ def test_saved_tuning_round_trips_without_a_gpu():
     for bad in (TuneChoice(3, 0, 0.0), TuneChoice(0, -1, 0.0), TuneChoice(1, 5000, 0.0)):
         assert lib.sc_tune_set(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
                                dims_arg((40, 36, 20)), ctypes.byref(bad)) == 1
+
+
+def _lib_stencil(coeffs: dict, hpow: int) -> "sc.Stencil":
+    """A library stencil in canonical form (sorted offsets, no zero weights,
+    reduced common denominator) from {offset: Fraction}."""
+    items = sorted((k, v) for k, v in coeffs.items() if v != 0)
+    den = 1
+    for _, v in items:
+        den = den * v.denominator // math.gcd(den, v.denominator)
+    s = sc.Stencil()
+    s.ndim = len(items[0][0])
+    s.npts = len(items)
+    s.hpow = hpow
+    s.radius = max(max(abs(c) for c in k) for k, _ in items)
+    nums = [int(v * den) for _, v in items]
+    g = den
+    for n_ in nums:
+        g = math.gcd(g, n_)
+    s.den = den // g
+    for i, ((k, _), n_) in enumerate(zip(items, nums)):
+        for a, c in enumerate(k):
+            s.off[i][a] = c
+        s.num[i] = n_ // g
+    return s
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_random_compositions_match_oracle(ndim):
+    """The library's exact composition on arbitrary rational stencils (not
+    only the paper's) equals the oracle's, point for point."""
+    rng = np.random.default_rng(40 + ndim)
+    for _ in range(8):
+        st_ = []
+        for radius, npts in ((3, 6), (2, 5)):
+            coeffs = {}
+            while len(coeffs) < npts:
+                off = tuple(int(v) for v in rng.integers(-radius, radius + 1, size=ndim))
+                coeffs[off] = Fraction(int(rng.integers(1, 10)) * (-1) ** int(rng.integers(0, 2)),
+                                       int(rng.integers(1, 13)))
+            st_.append((coeffs, int(rng.integers(0, 3))))
+        (ca, pa), (cb, pb) = st_
+        got = sc.compose_stencil(_lib_stencil(ca, pa), _lib_stencil(cb, pb))
+        want = ost.compose(ost.Stencil.make(ca, pa), ost.Stencil.make(cb, pb))
+        _same(got, want)
