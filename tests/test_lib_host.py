@@ -151,3 +151,39 @@ def test_random_compositions_match_oracle(ndim):
         got = sc.compose_stencil(_lib_stencil(ca, pa), _lib_stencil(cb, pb))
         want = ost.compose(ost.Stencil.make(ca, pa), ost.Stencil.make(cb, pb))
         _same(got, want)
+
+
+def test_random_weights_correctly_rounded():
+    """Weights of arbitrary rational stencils (numerators up to 10^6,
+    denominators up to 12) at arbitrary rational h (numerator and
+    denominator up to 10^4, h^-p with p up to 4, so every exact value fits
+    the documented 127 bits): FP64 and FP32 values bit-identical to the
+    oracle's correctly rounded exact rationals."""
+    rng = np.random.default_rng(77)
+    for _ in range(60):
+        ndim = int(rng.integers(1, 4))
+        coeffs = {}
+        while len(coeffs) < 5:
+            off = tuple(int(v) for v in rng.integers(-2, 3, size=ndim))
+            coeffs[off] = Fraction(int(rng.integers(-10 ** 6, 10 ** 6)) or 1, int(rng.integers(1, 13)))
+        hpow = int(rng.integers(0, 5))
+        s = _lib_stencil(coeffs, hpow)
+        os_ = ost.Stencil.make(coeffs, hpow)
+        hn, hd = int(rng.integers(1, 10 ** 4)), int(rng.integers(1, 10 ** 4))
+        keys = [k for k, _ in os_.coeffs]
+        for dt in (np.float64, np.float32):
+            w = sc.stencil_weights(s, hn, hd, dt)
+            ow = ost.fp_weights(os_, Fraction(hn, hd), dt)
+            want = np.array([ow[k] for k in keys], dtype=dt)
+            assert np.array_equal(w.view(np.uint64 if dt == np.float64 else np.uint32),
+                                  want.view(np.uint64 if dt == np.float64 else np.uint32)), (coeffs, hpow, hn, hd, dt)
+
+
+
+def test_weights_beyond_127_bits_report_overflow():
+    """An exact weight that needs more than 127 bits is refused with
+    SC_EOVERFLOW, not rounded from a wrapped value."""
+    s = _lib_stencil({(0,): Fraction(10 ** 15), (1,): Fraction(-1)}, 4)
+    with pytest.raises(sc.ScError) as e:
+        sc.stencil_weights(s, 1, 10 ** 6, np.float64)  # 10^15 * 10^24 > 2^127
+    assert e.value.status == 8  # SC_EOVERFLOW
