@@ -187,3 +187,36 @@ def test_weights_beyond_127_bits_report_overflow():
     with pytest.raises(sc.ScError) as e:
         sc.stencil_weights(s, 1, 10 ** 6, np.float64)  # 10^15 * 10^24 > 2^127
     assert e.value.status == 8  # SC_EOVERFLOW
+
+
+def test_random_add_and_embed_match_oracle():
+    """Sums of random rational stencils (with cancelling points) and 1D
+    stencils embedded along every axis: the library equals the oracle."""
+    rng = np.random.default_rng(91)
+    for _ in range(20):
+        ndim = int(rng.integers(1, 4))
+        hp = int(rng.integers(0, 3))
+        mk = []
+        for _s in range(2):
+            coeffs = {}
+            while len(coeffs) < (4 if ndim == 1 else 6):  # 5 offsets exist in 1D
+                off = tuple(int(v) for v in rng.integers(-2, 3, size=ndim))
+                coeffs[off] = Fraction(int(rng.integers(-9, 10)) or 2, int(rng.integers(1, 9)))
+            mk.append(coeffs)
+        k0 = next(iter(mk[0]))
+        mk[1][k0] = -mk[0][k0]  # one point cancels exactly
+        got = sc.stencil_add(_lib_stencil(mk[0], hp), _lib_stencil(mk[1], hp))
+        _same(got, ost.add(ost.Stencil.make(mk[0], hp), ost.Stencil.make(mk[1], hp)))
+        one_d = {(int(i),): Fraction(int(rng.integers(-9, 10)) or 1, int(rng.integers(1, 9)))
+                 for i in rng.choice(np.arange(-3, 4), size=4, replace=False)}
+        for axis in range(ndim):
+            got = sc.stencil_embed(_lib_stencil(one_d, hp), ndim, axis)
+            _same(got, ost.embed(ost.Stencil.make(one_d, hp), ndim, axis))
+
+
+def test_composition_overflow_is_refused():
+    """Products or sums beyond int64 are refused with SC_EOVERFLOW."""
+    big = _lib_stencil({(0,): Fraction(2 ** 40), (1,): Fraction(3)}, 0)
+    with pytest.raises(sc.ScError) as e:
+        sc.compose_stencil(big, big)  # 2^80
+    assert e.value.status == 8
