@@ -47,6 +47,15 @@ def stream_arg(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def require_device(name: str, t, dtype=None) -> None:
+    """Every device entry point takes contiguous CUDA tensors; anything else is
+    refused here, before the library could be handed a host address."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}")
+
+
 def apply_composed(s: Stencil, x: torch.Tensor, y: torch.Tensor, bc="periodic", h=(1, 1),
                    dims=None, stream=None) -> torch.Tensor:
     """y = A x with the composed stencil s (flat evaluation) on the device.
@@ -101,11 +110,14 @@ def apply_composition(outer: Stencil, inner: Stencil, x: torch.Tensor, y: torch.
     """y = outer(inner(x)): the composed operator in nested form (two passes
     through a device temporary); arith="pair" evaluates FP64 Laplacian
     factors in pairs of FP32 numbers."""
+    require_device("x", x)
+    require_device("y", y, x.dtype)
     if dims is None:
         dims = tuple(reversed(y.shape))
     nb = apply_composition_work_bytes(outer, inner, y.dtype, bc, dims)
     if work is None:
         work = torch.empty(max(nb, 1), dtype=torch.uint8, device=y.device)
+    require_device("work", work)
     check(lib.sc_apply_composition(ctypes.byref(outer), ctypes.byref(inner), dtype_code(y.dtype), bc_code(bc),
                                    dims_arg(dims), int(h[0]), int(h[1]), ctypes.c_void_p(x.data_ptr()),
                                    ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(work.data_ptr()),
@@ -137,6 +149,9 @@ lib.sc_tune_set.restype = ctypes.c_int
 
 
 def _tune_args(outer, inner, x, y, work, bc, h, dims):
+    require_device("x", x)
+    require_device("y", y, x.dtype)
+    require_device("work", work)
     if dims is None:
         dims = tuple(reversed(y.shape))
     return (ctypes.byref(outer), ctypes.byref(inner), dtype_code(y.dtype), bc_code(bc), dims_arg(dims),

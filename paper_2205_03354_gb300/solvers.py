@@ -7,7 +7,7 @@ import ctypes
 import torch
 
 from ._lib_loader import check, lib
-from .ops import stream_arg
+from .ops import require_device, stream_arg
 
 PREC_F64, PREC_MIXED, PREC_AUTO = 0, 1, 2
 SOLVER_PERSISTENT, SOLVER_PLAIN = 0, 1
@@ -64,6 +64,7 @@ lib.sc_ch_stats.restype = ctypes.c_int
 
 def _work(nbytes: int, device, work):
     if work is not None:
+        require_device("work", work)
         if work.numel() * work.element_size() < nbytes:
             raise ValueError("work buffer too small")
         return work
@@ -156,6 +157,7 @@ def ch_step(c: Ch, u: torch.Tensor, work=None, stream=None) -> list:
 
 def ch_stats(c: Ch, u: torch.Tensor, work=None, stream=None):
     """(mass[batch], energy[batch]) as Python lists."""
+    require_device("u", u, torch.float64)
     n = 1
     for a in range(c.ndim):
         n *= c.n[a]
@@ -176,6 +178,7 @@ lib.sc_ch_stats_noalloc.restype = ctypes.c_int
 def ch_stats_noalloc(c: Ch, u: torch.Tensor, stream=None):
     """sc_ch_stats without a work buffer (fixed library scratch, at most 2^24
     grid points per field; calls sharing a device must not overlap)."""
+    require_device("u", u, torch.float64)
     m = (ctypes.c_double * c.batch)()
     e = (ctypes.c_double * c.batch)()
     check(lib.sc_ch_stats_noalloc(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), m, e, stream_arg(stream)))
@@ -192,6 +195,7 @@ lib.sc_ch_run.restype = ctypes.c_int
 def ch_run(c: Ch, u: torch.Tensor, nsteps: int, use_graph=True, work=None, stream=None) -> list:
     """nsteps IMEX steps of every field of u in place; returns per-step lists
     of per-field info dicts."""
+    require_device("u", u, torch.float64)
     nb = int(lib.sc_ch_run_work_bytes(ctypes.byref(c), nsteps))
     w = _work(nb, u.device, work)
     infos = (SolveInfo * (nsteps * c.batch))()
