@@ -91,3 +91,69 @@ def test_cg_zero_rhs_and_x0():
     b = np.arange(1.0, 6.0)
     x, it, res, ok = cg(lambda v: 2 * v, b, b / 2)
     assert ok and it == 0 and np.allclose(x, b / 2)
+
+
+def _random_one_sided(ndim, seed):
+    """A stencil with random weights on an asymmetric set of offsets (radius
+    2, some axes reaching further one way than the other), so that a swapped
+    axis, a flipped sign or a ghost ring offset by one shows up."""
+    rng = np.random.default_rng(seed)
+    coeffs = {}
+    for _ in range(9):
+        off = tuple(int(v) for v in rng.integers(-1, 3, ndim))
+        coeffs[off] = Fraction(int(rng.integers(1, 50)) * (1 if rng.random() < 0.5 else -1), 7)
+    coeffs[(2,) + (0,) * (ndim - 1)] = Fraction(3)  # reach radius 2 along x only
+    return st.Stencil.make(coeffs, 0)
+
+
+def _edge_points(shape, rng, nrand):
+    """Every corner of the grid, points on every face and edge, and random
+    interior points (array-axis order)."""
+    pts = set()
+    lo_hi = [(0, 1, n - 2, n - 1) for n in shape]
+    for p in np.ndindex(*(4,) * len(shape)):
+        pts.add(tuple(lo_hi[a][p[a]] for a in range(len(shape))))
+    for _ in range(nrand):
+        pts.add(tuple(int(rng.integers(0, n)) for n in shape))
+    return np.array(sorted(pts))
+
+
+@pytest.mark.parametrize("ndim,shape", [(2, (9, 13)), (3, (6, 7, 9))])
+def test_apply_at_matches_apply_every_boundary(ndim, shape):
+    """apply_at (one point at a time) against the whole-grid apply for every
+    boundary treatment, on one-sided stencils (forward-difference outer
+    products and random asymmetric ones), at every corner, face and edge and
+    at random points: the same sum, so agreement to 1e-15 of sum |w x|."""
+    rng = np.random.default_rng(31 + ndim)
+    stencils = [_random_one_sided(ndim, 5 + ndim)]
+    if ndim == 2:
+        stencils.append(st.outer_product(st.d1_forward(), st.d2_forward()))
+    else:
+        stencils.append(st.outer_product(st.outer_product(st.d1_forward(), st.d2_forward()), st.d1_forward()))
+    for s in stencils:
+        w = {k: float(v) for k, v in s.coeffs}
+        R = s.radius
+        absw = {k: abs(v) for k, v in w.items()}
+        for bc in ("periodic", "zero", "ghosted"):
+            xshape = tuple(n + 2 * R for n in shape) if bc == "ghosted" else shape
+            x = rng.uniform(-1, 1, xshape)
+            full = ap.apply(w, x, bc, R)
+            assert full.shape == shape
+            pts = _edge_points(shape, rng, 40)
+            got = ap.apply_at(w, x, bc, pts, R)
+            ref = full[tuple(pts.T)]
+            scale = ap.apply(absw, np.abs(x), bc, R)[tuple(pts.T)]
+            assert np.all(np.abs(got - ref) <= 1e-15 * scale), (bc, s)
+
+
+def test_apply_at_hand_computed_values():
+    """Values worked out by hand: a forward difference in x at the last
+    column reads the wrapped first column (periodic), nothing (zero), or the
+    ghost ring (ghosted)."""
+    w = {(1, 0): 1.0, (0, 0): -1.0}  # (x_{i+1} - x_i), offsets in (dx, dy) order
+    x = np.arange(12.0).reshape(3, 4)  # rows y, columns x
+    pt = np.array([[1, 3]])  # y = 1, x = 3 (last column)
+    assert ap.apply_at(w, x, "periodic", pt)[0] == x[1, 0] - x[1, 3]
+    assert ap.apply_at(w, x, "zero", pt)[0] == -x[1, 3]
+    xg = np.arange(30.0).reshape(5, 6)  # 3 x 4 interior with a ring of width 1
+    assert ap.apply_at(w, xg, "ghosted", pt, 1)[0] == xg[2, 5] - xg[2, 4]

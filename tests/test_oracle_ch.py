@@ -57,3 +57,50 @@ def test_double_well_matches_closed_form():
     assert ok and np.max(np.abs(cn - cf)) < 1e-10
     # f' of the double well vanishes at the wells and the barrier top
     assert np.allclose(ch.fprime(np.array([0.3, 0.5, 0.7]), chem), 0.0)
+
+
+def _chem_sum_cos_mode(A, N, chem):
+    """sum_i f(A cos(2 pi k i / N)) for a mode with k, 2k, 3k, 4k all nonzero
+    mod N, from sum cos = sum cos^3 = 0, sum cos^2 = N/2, sum cos^4 = 3N/8."""
+    s2, s4 = N / 2.0, 3.0 * N / 8.0
+    if chem[0] == "cubic":  # (u^4 - 2u^2 + 1) / 4
+        return (A ** 4 * s4 - 2.0 * A ** 2 * s2 + N) / 4.0
+    _, rho, ca, cb = chem  # rho ((u^2 - (ca+cb) u + ca cb))^2, odd powers drop
+    return rho * (A ** 4 * s4 + ((ca + cb) ** 2 + 2.0 * ca * cb) * A ** 2 * s2 + (ca * cb) ** 2 * N)
+
+
+@pytest.mark.parametrize("chem", [("cubic",), ("double_well", 5.0, 0.3, 0.7)])
+def test_free_energy_of_constant_fields(chem):
+    """A constant field has no gradient energy: F = h^d N^d f(c), with f known
+    at its wells and elsewhere by hand (cubic: f(0) = 1/4, f(+-1) = 0,
+    f(2) = 9/4; double well rho 5, ca .3, cb .7: f(ca) = f(cb) = 0,
+    f(0.5) = 5 * 0.2^4, f(0) = 5 * 0.09 * 0.49)."""
+    if chem[0] == "cubic":
+        table = {0.0: 0.25, 1.0: 0.0, -1.0: 0.0, 2.0: 2.25}
+    else:
+        table = {0.3: 0.0, 0.7: 0.0, 0.5: 5 * 0.2 ** 4, 0.0: 5 * 0.09 * 0.49}
+    for ndim, n, h in [(2, 12, 0.37), (3, 6, 2.5)]:
+        for c, f in table.items():
+            u = np.full((n,) * ndim, c)
+            F = ch.free_energy(u, h, 1.7, chem)
+            assert abs(F - h ** ndim * n ** ndim * f) <= 1e-13 * max(1.0, h ** ndim * n ** ndim * f), (c, F)
+
+
+@pytest.mark.parametrize("chem", [("cubic",), ("double_well", 5.0, 0.3, 0.7)])
+@pytest.mark.parametrize("ndim,n,k,h,kappa,A", [(2, 16, 3, 0.25, 2.0, 0.8), (3, 10, 1, 1.5, 0.3, 1.3)])
+def test_free_energy_of_a_fourier_mode(chem, ndim, n, k, h, kappa, A):
+    """u = A cos(2 pi k i / N) along one axis at a time: the forward-difference
+    gradient sum is N^(d-1) A^2 N (2 sin(pi k / N) / h)^2 / 2, so
+    F = h^d [ (kappa/2) N^(d-1) A^2 N (2 sin(pi k/N)/h)^2 / 2 + N^(d-1) sum_i f ]
+    with sum_i f from the power sums of cos.  A kappa-for-kappa/2 slip, a
+    missing h^d or a backward/central difference all break it."""
+    grad = n ** (ndim - 1) * A ** 2 * n * (2.0 * np.sin(np.pi * k / n) / h) ** 2 / 2.0
+    chem_sum = n ** (ndim - 1) * _chem_sum_cos_mode(A, n, chem)
+    expect = h ** ndim * (0.5 * kappa * grad + chem_sum)
+    i = np.arange(n)
+    for ax in range(ndim):
+        shape = [1] * ndim
+        shape[ax] = n
+        u = np.broadcast_to((A * np.cos(2 * np.pi * k * i / n)).reshape(shape), (n,) * ndim).copy()
+        F = ch.free_energy(u, h, kappa, chem)
+        assert abs(F - expect) <= 1e-12 * abs(expect), (ax, F, expect)
