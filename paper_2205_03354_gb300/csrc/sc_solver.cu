@@ -247,7 +247,8 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
   }
   P.p = cv.take(npts * ti);
   P.q = cv.take(npts * ti);
-  P.part = static_cast<double *>(cv.take(size_t(3) * P.nslot * 8));
+  // two buffers of 3 * nslot partials, alternating by reduction parity
+  P.part = static_cast<double *>(cv.take(size_t(6) * P.nslot * 8));
   P.scal = static_cast<double *>(cv.take(8 * 8));
   P.bar = static_cast<unsigned *>(cv.take(16));
   P.st = static_cast<SolveState *>(cv.take(sizeof(SolveState)));

@@ -11,9 +11,10 @@
 //   B:  d += alpha p, rh -= alpha q    chunked vector pass; partial rh.rh
 //   C:  p = rh + beta p                chunked vector pass
 // with a group barrier after each phase.  Reductions are deterministic: every
-// tile/chunk writes its partial to a fixed slot and the last CTA to arrive at
-// the barrier sums the slots in index order, so a problem's result does not
-// depend on its group size or on the rest of the batch.
+// tile/chunk writes its partial to a fixed slot and the slots are summed in
+// index order (by every CTA of a small group, by the last CTA to arrive in a
+// large one), so a problem's result does not depend on its group size or on
+// the rest of the batch.
 //
 // Mixed precision (TI = float): FP32 stencil applies and vector updates; the
 // FP64 solution x, right-hand side and true residual r = rhs - A x are kept in
@@ -87,6 +88,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 // i < nused) in index order; the sums are returned in out[0..nval-1] in every
 // CTA of the group.  Returns false when a wait timed out (the problem is then
 // marked SC_ETIMEOUT and every CTA of the group leaves).
+//
+// The partial slots are double-buffered by the parity of the reduction's
+// sequence number: the phase before reduction k writes buffer k & 1 and the
+// reduction reads it.  In the small-group protocol every CTA reads the slots
+// after the arrival count alone, so a CTA that finished reading may already
+// write the next phase's partials while a slower one still reads; those go to
+// the other buffer, and no CTA can write buffer k & 1 again before every CTA
+// has arrived at reduction k + 1, i.e. finished reading reduction k.
 struct GroupCtx {
   const SolveProb *P;
   int rank;
@@ -95,7 +104,13 @@ struct GroupCtx {
   double *red;      // shared scratch (>= CG_NTHR/32 doubles)
   int *flag;        // shared int
   long long spin_limit = SPIN_LIMIT;
+  unsigned nred = 0;  // reductions completed in this launch (selects the slot buffer)
 };
+
+// The partial slots the next reduction of this group reads (3 * nslot values).
+__device__ __forceinline__ double *cur_part(const GroupCtx &G) {
+  return G.P->part + (G.nred & 1u) * 3LL * G.P->nslot;
+}
 
 __device__ __forceinline__ double fixed_sum(const double *a, int n, double *red) {
   // thread t adds slots t, t + 128, ... in order; 8 loads in flight
@@ -124,13 +139,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *out,
                              unsigned long long deadline = 0ull) {
   const SolveProb &P = *G.P;
+  const double *part = cur_part(G);
   __shared__ double s_out[4];
   __syncthreads();
   bool ok = true;
   if (P.ncta == 1) {
     for (int k = 0; k < nval; ++k) {
       __threadfence_block();
-      double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
+      double v = fixed_sum(part + (long long)k * P.nslot, nused, G.red);
       if (threadIdx.x == 0) s_out[k] = v;
     }
     if (deadline && threadIdx.x == 0) s_out[3] = global_ns() >= deadline ? 1.0 : 0.0;
@@ -163,7 +179,7 @@ __device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *ou
     } else {
       __threadfence();
       for (int k = 0; k < nval; ++k) {
-        const double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
+        const double v = fixed_sum(part + (long long)k * P.nslot, nused, G.red);
         if (threadIdx.x == 0) s_out[k] = v;
       }
     }
@@ -180,7 +196,7 @@ __device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *ou
     if (*G.flag) {  // last to arrive: reduce in fixed order and publish
       __threadfence();
       for (int k = 0; k < nval; ++k) {
-        double v = fixed_sum(P.part + (long long)k * P.nslot, nused, G.red);
+        double v = fixed_sum(part + (long long)k * P.nslot, nused, G.red);
         if (threadIdx.x == 0) P.scal[k] = v;
       }
       if (deadline && threadIdx.x == 0) P.scal[3] = global_ns() >= deadline ? 1.0 : 0.0;
@@ -216,6 +232,7 @@ __device__ inline bool group_reduce(GroupCtx &G, int nval, int nused, double *ou
   }
   for (int k = 0; k < nval; ++k) out[k] = s_out[k];
   if (deadline) out[3] = s_out[3];
+  G.nred += 1;
   __syncthreads();
   return ok;
 }
@@ -316,7 +333,7 @@ struct CgWeights {
 // Phase A: q = A p over the group's tiles.
 template <typename T, int NDIM, int R>
 __device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, double *red,
-                            const CgWeights &cw) {
+                            const CgWeights &cw, double *part) {
   using K = FlatApply<T, NDIM, R, CLS_CROSS2, 1>;
   const ApplyGeom g = cg_geom<T, NDIM, R>(P, P.H_in);
   const WBox<T, NDIM, R> &W = *reinterpret_cast<const WBox<T, NDIM, R> *>(
@@ -328,7 +345,7 @@ __device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, d
                                    g.out_ss, P.nx, T(P.a), T(P.b), T(0)};
     K::run_tile(static_cast<const T *>(P.p), g, W, x0, y0, z0, reinterpret_cast<T *>(smem), epi);
     const double s = block_sum<CG_NTHR>(double(epi.dot), red);
-    if (threadIdx.x == 0) P.part[tile] = s;
+    if (threadIdx.x == 0) part[tile] = s;
   }
 }
 
@@ -336,7 +353,7 @@ __device__ void phase_apply(const SolveProb &P, int rank, unsigned char *smem, d
 // (when mean_fix) partial sum(x) in slot 1.
 template <int NDIM, int R>
 __device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, double *red,
-                            const CgWeights &cw) {
+                            const CgWeights &cw, double *part) {
   using K = FlatApply<double, NDIM, R, CLS_CROSS2, 1>;
   const ApplyGeom g = cg_geom<double, NDIM, R>(P, P.H_64);
   const WBox<double, NDIM, R> &W = *reinterpret_cast<const WBox<double, NDIM, R> *>(cw.w64);
@@ -346,7 +363,7 @@ __device__ void phase_resid(const SolveProb &P, int rank, unsigned char *smem, d
     ResidEpi<NDIM, K::VX> epi{P.x, P.rhs, P.r, g.out_sy, g.out_ss, P.nx, P.a, P.b, 0.0};
     K::run_tile(P.x, g, W, x0, y0, z0, reinterpret_cast<double *>(smem), epi);
     const double s = block_sum<CG_NTHR>(epi.dot, red);
-    if (threadIdx.x == 0) P.part[tile] = s;
+    if (threadIdx.x == 0) part[tile] = s;
   }
 }
 
@@ -424,7 +441,7 @@ __device__ __forceinline__ void vec_elems(const SolveProb &P, long long i, int n
 }
 
 template <typename TI, int KIND>
-__device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) {
+__device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red, double *part) {
   TI *rh = static_cast<TI *>(P.rh), *p = static_cast<TI *>(P.p), *q = static_cast<TI *>(P.q),
      *d = static_cast<TI *>(P.d);
   for (int c = rank; c < P.nchunks; c += P.ncta) {
@@ -556,12 +573,12 @@ __device__ void phase_vec(const SolveProb &P, int rank, double s1, double *red) 
     }
     if (KIND == 0 || KIND == 1 || KIND == 4 || KIND == 5) {
       const double t0 = block_sum<CG_NTHR>(a0 + double(acc_t), red);
-      if (threadIdx.x == 0) P.part[c] = t0;
+      if (threadIdx.x == 0) part[c] = t0;
       if (KIND == 0) {
         const double t1 = block_sum<CG_NTHR>(a1, red);
-        if (threadIdx.x == 0) P.part[P.nslot + c] = t1;
+        if (threadIdx.x == 0) part[P.nslot + c] = t1;
         const double t2 = block_sum<CG_NTHR>(a2, red);
-        if (threadIdx.x == 0) P.part[2 * P.nslot + c] = t2;
+        if (threadIdx.x == 0) part[2 * P.nslot + c] = t2;
       }
     }
   }
@@ -600,9 +617,9 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
 
   if (phase == 0) {
     // r = rhs - A x0 (FP64); rh = r; p = rh
-    phase_resid<NDIM, R>(P, G.rank, smem, red, cw);
+    phase_resid<NDIM, R>(P, G.rank, smem, red, cw, cur_part(G));
     if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
-    phase_vec<TI, 0>(P, G.rank, 0.0, red);
+    phase_vec<TI, 0>(P, G.rank, 0.0, red, cur_part(G));
     if (!group_reduce(G, 3, P.nchunks, red_out)) return;
     rr = red_out[0];
     bnorm = sqrt(red_out[1]);
@@ -622,7 +639,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
       break;
     }
     // A: q = A p, p.q
-    phase_apply<TI, NDIM, R>(P, G.rank, smem, red, cw);
+    phase_apply<TI, NDIM, R>(P, G.rank, smem, red, cw, cur_part(G));
     if (!group_reduce(G, 1, P.ntiles_in, red_out)) return;
     const double pq = red_out[0];
     if (!finite_pos(pq) || !(rr == rr)) {
@@ -632,7 +649,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
     }
     const double alpha = rr / pq;
     // B: d += alpha p, rh -= alpha q, rh.rh
-    phase_vec<TI, 1>(P, G.rank, alpha, red);
+    phase_vec<TI, 1>(P, G.rank, alpha, red, cur_part(G));
     if (!group_reduce(G, 1, P.nchunks, red_out)) return;
     double rr_new = red_out[0];
     ++iters;
@@ -649,10 +666,10 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
     const bool refresh = P.mixed ? (rn <= P.delta * rmax || rn <= tol * bnorm) : (rn <= tol * bnorm);
     if (refresh) {
       if (P.mixed) {  // x += d in FP64
-        phase_vec<TI, 3>(P, G.rank, 0.0, red);
+        phase_vec<TI, 3>(P, G.rank, 0.0, red, cur_part(G));
         if (!group_reduce(G, 0, 0, red_out)) return;
       }
-      phase_resid<NDIM, R>(P, G.rank, smem, red, cw);
+      phase_resid<NDIM, R>(P, G.rank, smem, red, cw, cur_part(G));
       if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
       ++outer;
       rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
@@ -661,7 +678,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
         break;
       }
       if (P.mixed) {
-        phase_vec<TI, 4>(P, G.rank, 0.0, red);
+        phase_vec<TI, 4>(P, G.rank, 0.0, red, cur_part(G));
         if (!group_reduce(G, 1, P.nchunks, red_out)) return;
         rr_new = red_out[0];
       } else {
@@ -672,7 +689,7 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
     beta = rr_new / rr;
     rr = rr_new;
     // C: p = rh + beta p
-    phase_vec<TI, 2>(P, G.rank, beta, red);
+    phase_vec<TI, 2>(P, G.rank, beta, red, cur_part(G));
     if (!group_reduce(G, 0, 0, red_out, deadline)) return;
     if (deadline && red_out[3] != 0.0) break;
   }
@@ -680,17 +697,17 @@ __device__ void cg_run(GroupCtx &G, unsigned char *smem, long long budget,
   if (phase == 3) {
     // finish: FP64 x (mixed: fold d), optional mean fix, true residual
     if (P.mixed) {
-      phase_vec<TI, 3>(P, G.rank, 0.0, red);
+      phase_vec<TI, 3>(P, G.rank, 0.0, red, cur_part(G));
       if (!group_reduce(G, 0, 0, red_out)) return;
     }
     if (P.mean_fix) {
-      phase_vec<TI, 5>(P, G.rank, 0.0, red);
+      phase_vec<TI, 5>(P, G.rank, 0.0, red, cur_part(G));
       if (!group_reduce(G, 1, P.nchunks, red_out)) return;
       const double c = (sumb - red_out[0]) / double(P.npts);
-      phase_vec<TI, 6>(P, G.rank, c, red);
+      phase_vec<TI, 6>(P, G.rank, c, red, cur_part(G));
       if (!group_reduce(G, 0, 0, red_out)) return;
     }
-    phase_resid<NDIM, R>(P, G.rank, smem, red, cw);
+    phase_resid<NDIM, R>(P, G.rank, smem, red, cw, cur_part(G));
     if (!group_reduce(G, 1, P.ntiles_64, red_out)) return;
     rel = bnorm > 0 ? sqrt(red_out[0]) / bnorm : 0.0;
     if (status == SC_OK && !(rel <= tol)) {

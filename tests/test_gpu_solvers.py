@@ -102,6 +102,33 @@ def test_batch_equals_alone():
         assert torch.equal(a, b)
 
 
+def test_many_small_batch_repeated_equals_alone():
+    """Many small plate problems in one persistent launch, where every CTA
+    group takes the small-group reduction (each CTA sums the partial slots
+    itself after the arrival count): repeated launches give the bits of the
+    solo solves every time, so no CTA reads partial slots that a faster CTA
+    of its group has already overwritten with the next phase's values."""
+    rng = np.random.default_rng(77)
+    specs = [(int(rng.integers(8, 40)), "f64" if k % 3 else "mixed") for k in range(48)]
+    alone, probs, xs, keep = [], [], [], []
+    for k, (n, prec) in enumerate(specs):
+        m, f, g, x = bvp_inputs(n, 2, ks=(1 + k % 3, 1 + (k // 3) % 2))
+        info = sc.solve_biharmonic(f, g, x, prec=prec, rtol=RTOL)
+        assert info["status"] == 0 and info["rel_res"] <= RTOL
+        alone.append(x.clone())
+        keep.append((f, g))
+    for rep in range(3):
+        probs, xs = [], []
+        for (f, g), a, (n, prec) in zip(keep, alone, specs):
+            x2 = torch.full_like(a, np.nan)
+            probs.append(sc.make_bvp(f, g, x2, prec=prec, rtol=RTOL))
+            xs.append(x2)
+        infos = sc.solve_biharmonic_batch(probs)
+        for a, b, info in zip(alone, xs, infos):
+            assert info["status"] == 0 and info["rel_res"] <= RTOL, (rep, info)
+            assert torch.equal(a, b), rep
+
+
 def test_iteration_cap_reports_not_converged():
     m, f, g, x = bvp_inputs(32, 2)
     with pytest.raises(sc.ScError):
