@@ -227,6 +227,23 @@ static size_t elems_ext(int ndim, const int64_t *dims, int ext) {
   return n;
 }
 
+size_t grid_elems_ext(int ndim, const int64_t *dims, int ext) { return elems_ext(ndim, dims, ext); }
+
+bool spans_overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+  return na && nb && a0 < b0 + nb && b0 < a0 + na;
+}
+
+int check_disjoint(int ndim, int bc, const int64_t *dims, int r_in, size_t es, const void *x, const void *y,
+                   const void *work, size_t work_bytes) {
+  const size_t xb = elems_ext(ndim, dims, bc == SC_BC_GHOSTED ? r_in : 0) * es;
+  const size_t yb = elems_ext(ndim, dims, 0) * es;
+  if (spans_overlap(x, xb, y, yb)) return fail(SC_EINVAL, "x and y must not overlap");
+  if (work && (spans_overlap(work, work_bytes, x, xb) || spans_overlap(work, work_bytes, y, yb)))
+    return fail(SC_EINVAL, "the work space must not overlap x or y");
+  return SC_OK;
+}
+
 size_t composition_work_bytes(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims) {
   const size_t es = dtype == SC_F64 ? 8 : 4;
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
@@ -318,7 +335,7 @@ int sc_apply_composed(const sc_stencil *s, int32_t dtype, int32_t bc, const int6
                       sc_stream_t stream) {
   if (int rc = validate_apply(s, dtype, bc, dims, h_num, h_den)) return rc;
   if (!x_dev || !y_dev) return fail(SC_EINVAL, "null device pointer");
-  if (x_dev == y_dev) return fail(SC_EINVAL, "x and y must not overlap");
+  if (int rc = check_disjoint(s->ndim, bc, dims, s->radius, dtype == SC_F64 ? 8 : 4, x_dev, y_dev)) return rc;
   ApplyReq q{s, dtype, bc, dims, h_num, h_den, x_dev, y_dev};
   int rc = apply_enqueue(q, (cudaStream_t)stream);
   if (!rc) clear_error();
@@ -342,9 +359,11 @@ int sc_apply_composition(const sc_stencil *outer, const sc_stencil *inner, int32
   if (outer->radius + inner->radius > SC_MAX_APPLY_RADIUS)
     return fail(SC_EINVAL, "composed radius %d > %d", outer->radius + inner->radius, SC_MAX_APPLY_RADIUS);
   if (!x_dev || !y_dev || !work_dev) return fail(SC_EINVAL, "null device pointer");
-  if (x_dev == y_dev) return fail(SC_EINVAL, "x and y must not overlap");
   const size_t need = composition_work_bytes(outer, inner, dtype, bc, dims);
   if (work_bytes < need) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, need);
+  if (int rc = check_disjoint(outer->ndim, bc, dims, outer->radius + inner->radius, dtype == SC_F64 ? 8 : 4,
+                              x_dev, y_dev, work_dev, need))
+    return rc;
   int rc = composition_enqueue(outer, inner, dtype, bc, dims, h_num, h_den, x_dev, y_dev, work_dev,
                                (cudaStream_t)stream, arith);
   if (!rc) clear_error();

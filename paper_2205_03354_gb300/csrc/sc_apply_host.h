@@ -31,6 +31,14 @@ int validate_apply(const sc_stencil *s, int dtype, int bc, const int64_t *dims, 
 // Enqueues y = A x on `st` (no validation of pointers).
 int apply_enqueue(const ApplyReq &q, cudaStream_t st);
 size_t grid_elems(const sc_stencil *s, int bc, const int64_t *dims, bool input);
+// Elements of a grid of `dims` extended by `ext` on every side of every axis.
+size_t grid_elems_ext(int ndim, const int64_t *dims, int ext);
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool spans_overlap(const void *a, size_t na, const void *b, size_t nb);
+// SC_EINVAL unless x (input extent for radius `r_in` under `bc`), y (the
+// output grid) and, when given, the work space are pairwise disjoint.
+int check_disjoint(int ndim, int bc, const int64_t *dims, int r_in, size_t es, const void *x, const void *y,
+                   const void *work = nullptr, size_t work_bytes = 0);
 int num_sms();
 // Planes per CTA for a streamed launch of `tiles_xy` tiles per plane over
 // `nplanes` planes with halo R, given `slots` = resident CTAs per SM x SMs:

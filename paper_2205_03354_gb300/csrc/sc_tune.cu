@@ -69,9 +69,12 @@ int sc_autotune_apply(const sc_stencil *outer, const sc_stencil *inner, int32_t 
   if (int rc = validate_apply(outer, dtype, bc, dims, h_num, h_den)) return rc;
   if (int rc = validate_apply(inner, dtype, bc, dims, h_num, h_den)) return rc;
   if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
-  if (!x_dev || !y_dev || !work_dev || x_dev == y_dev) return fail(SC_EINVAL, "bad device pointers");
-  if (work_bytes < composition_work_bytes(outer, inner, dtype, bc, dims))
-    return fail(SC_ENOMEM, "work space too small");
+  if (!x_dev || !y_dev || !work_dev) return fail(SC_EINVAL, "bad device pointers");
+  const size_t need = composition_work_bytes(outer, inner, dtype, bc, dims);
+  if (work_bytes < need) return fail(SC_ENOMEM, "work space too small");
+  if (int rc = check_disjoint(outer->ndim, bc, dims, outer->radius + inner->radius, dtype == SC_F64 ? 8 : 4,
+                              x_dev, y_dev, work_dev, need))
+    return rc;
   sc_stencil C;
   if (int rc = sc_compose_stencil(outer, inner, &C)) return rc;
   if (C.radius > SC_MAX_APPLY_RADIUS) return fail(SC_EINVAL, "composed radius too large");
@@ -138,7 +141,10 @@ int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dty
   if (int rc = validate_apply(outer, dtype, bc, dims, h_num, h_den)) return rc;
   if (int rc = validate_apply(inner, dtype, bc, dims, h_num, h_den)) return rc;
   if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
-  if (!x_dev || !y_dev || x_dev == y_dev) return fail(SC_EINVAL, "bad device pointers");
+  if (!x_dev || !y_dev) return fail(SC_EINVAL, "bad device pointers");
+  if (int rc = check_disjoint(outer->ndim, bc, dims, outer->radius + inner->radius, dtype == SC_F64 ? 8 : 4,
+                              x_dev, y_dev))
+    return rc;
   sc_tune_choice c;
   std::memset(&c, 0, sizeof(c));
   bool have = false;
@@ -153,6 +159,10 @@ int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dty
   if (!have) c.eval = SC_EVAL_FLAT;  // untuned: the composed weights, model depth
   if (c.eval != SC_EVAL_FLAT && (!work_dev || work_bytes < composition_work_bytes(outer, inner, dtype, bc, dims)))
     return fail(SC_ENOMEM, "work space too small for the tuned schedule");
+  if (c.eval != SC_EVAL_FLAT)
+    if (int rc = check_disjoint(outer->ndim, bc, dims, outer->radius + inner->radius, dtype == SC_F64 ? 8 : 4,
+                                x_dev, y_dev, work_dev, composition_work_bytes(outer, inner, dtype, bc, dims)))
+      return rc;
   sc_stencil C;
   if (int rc = sc_compose_stencil(outer, inner, &C)) return rc;
   int rc = run_choice(outer, inner, &C, dtype, bc, dims, h_num, h_den, x_dev, y_dev, work_dev, c,

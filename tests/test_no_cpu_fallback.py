@@ -64,3 +64,33 @@ def test_host_buffer_entry_point_refuses_without_device_work():
     with pytest.raises(ValueError):
         sc.apply_composed_host(sc.compose_stencil(L, L), torch.from_numpy(x), torch.from_numpy(x.copy()),
                                torch.zeros(1 << 16, dtype=torch.uint8), h=(1, 16))
+
+
+def test_overlapping_device_ranges_are_refused_before_any_launch():
+    """x and y (and a work space) must be disjoint byte ranges, not merely
+    different pointers: y starting inside x's ghosted extent, or a work space
+    overlapping either, is refused with SC_EINVAL.  The addresses are never
+    dereferenced (the check runs before anything is enqueued)."""
+    import ctypes
+
+    from paper_2205_03354_gb300._lib_loader import lib
+    from paper_2205_03354_gb300.ops import dims_arg
+
+    L = sc.laplacian(2, 4)
+    B = sc.compose_stencil(L, L)
+    dims = dims_arg((64, 64))
+    base = 1 << 40
+    # ghosted input (64 + 8)^2 doubles; y placed 8 bytes before its end
+    x = base
+    y = base + (72 * 72 - 1) * 8
+    rc = lib.sc_apply_composed(ctypes.byref(B), 0, 1, dims, 1, 64, ctypes.c_void_p(x), ctypes.c_void_p(y), None)
+    assert rc == 1  # SC_EINVAL
+    # the same y is fine for a periodic input of 64^2 doubles only if it lies beyond it
+    y2 = base + 64 * 64 * 8 - 8
+    rc = lib.sc_apply_composed(ctypes.byref(B), 0, 0, dims, 1, 64, ctypes.c_void_p(x), ctypes.c_void_p(y2), None)
+    assert rc == 1
+    y3 = base + 64 * 64 * 8 * 2  # disjoint x and y; the work space starts inside y
+    rc = lib.sc_apply_composition(ctypes.byref(L), ctypes.byref(L), 0, 0, dims, ctypes.c_int64(1), ctypes.c_int64(64),
+                                  ctypes.c_void_p(x), ctypes.c_void_p(y3), ctypes.c_void_p(y3 + 64),
+                                  ctypes.c_size_t(1 << 30), 0, None)
+    assert rc == 1
