@@ -346,11 +346,18 @@ int sc_ch_stats(const sc_ch *p, const double *u_dev, double *mass_host, double *
  * it until the process exits; fields of more than 2^24 grid points are
  * rejected with SC_EINVAL.  The first call on a device looks the array's
  * device address up (cudaGetSymbolAddress) with that device current and
- * should happen outside any stream capture.  All calls share the array:
- * calls that may overlap on the GPU (other streams or host threads) race and
- * must be serialised by the caller.  Allocates nothing. */
+ * should happen outside any stream capture; the address is kept for later
+ * calls on that device.  All calls share the array: calls that may overlap
+ * on the GPU (other streams or host threads) race and must be serialised by
+ * the caller.  Allocates nothing. */
 int sc_ch_stats_noalloc(const sc_ch *p, const double *u_dev, double *mass_host, double *energy_host,
                         sc_stream_t stream);
+
+/* Drops the device addresses sc_ch_stats_noalloc kept.  A process that calls
+ * cudaDeviceReset on a device must call this afterwards, before the next
+ * sc_ch_stats_noalloc on that device: the reset ends the context the kept
+ * address belonged to.  Host-only; no device call. */
+void sc_noalloc_forget(void);
 
 
 /* Failure-detection self-test of the solver's bounded group barrier: runs

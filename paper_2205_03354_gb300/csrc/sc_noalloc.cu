@@ -14,8 +14,12 @@
 //    that uses it until the process exits (STATS_SCRATCH doubles, 64 KiB);
 //  * host code cannot use the array's name as a device address, so the first
 //    call on each device looks the address up with cudaGetSymbolAddress
-//    while that device is current; make that first call outside any stream
-//    capture;
+//    while that device is current and keeps it for later calls; make that
+//    first call outside any stream capture;
+//  * the kept address belongs to the device's context at the first call: a
+//    process that calls cudaDeviceReset on a device gets a new context in
+//    which the array may sit elsewhere, so it must call sc_noalloc_forget()
+//    after the reset (the next call then looks the address up again);
 //  * every call on a device shares the one array and it keeps the previous
 //    call's contents: each call writes every slot it later reads, so nothing
 //    has to start at zero, but two calls that can run on the GPU at the same
@@ -65,6 +69,11 @@ static int scratch_address(double **out) {
 using namespace sc;
 
 extern "C" {
+
+void sc_noalloc_forget(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (int d = 0; d < MAX_DEVICES; ++d) g_scratch_ptr[d] = nullptr;
+}
 
 int sc_ch_stats_noalloc(const sc_ch *c, const double *u_dev, double *mass_host, double *energy_host,
                         sc_stream_t stream) {

@@ -185,6 +185,15 @@ def ch_stats_noalloc(c: Ch, u: torch.Tensor, stream=None):
     return list(m), list(e)
 
 
+lib.sc_noalloc_forget.argtypes = []
+lib.sc_noalloc_forget.restype = None
+
+
+def noalloc_forget():
+    """Drop the kept scratch addresses (call after cudaDeviceReset)."""
+    lib.sc_noalloc_forget()
+
+
 lib.sc_ch_run_work_bytes.argtypes = [_CP, ctypes.c_int64]
 lib.sc_ch_run_work_bytes.restype = ctypes.c_size_t
 lib.sc_ch_run.argtypes = [_CP, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,

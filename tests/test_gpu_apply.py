@@ -1,6 +1,6 @@
 """GPU parity of the composed-stencil apply against the FP64 oracle.
 
-Tolerances (derived from the arithmetic):
+Tolerances (derived from the arithmetic of each schedule):
   * FP64: normwise ||y - y_ref||_2 <= 1e-12 ||y_ref||_2 on random fields, and
     elementwise |y - y_ref| <= npts * eps64 * sum_k |w_k x_{i+k}|;
   * FP32 (inputs and weights rounded to float32, accumulation in float32):
@@ -116,32 +116,86 @@ def test_host_buffer_entry_point_matches_device_one():
     assert torch.equal(yd.cpu(), y)
 
 
-@pytest.mark.parametrize("ndim,n,dt", [(2, 8192, np.float32), (2, 8192, np.float64),
-                                       (3, 512, np.float32), (3, 512, np.float64)])
-def test_full_size_sampled(ndim, n, dt):
-    """The apply-sweep sizes in the launch configuration the bench times,
-    checked on 400 sampled points (incl. edges and corners) against the
+# every evaluation schedule the apply sweep can launch at its full sizes, with
+# the planes per CTA (halo-blocking depth) the sweep's tuning chose for it
+FULL_SIZE_SCHEDULES = [
+    (2, 8192, np.float64, "pair", 32), (2, 8192, np.float64, "flat", 0),
+    (2, 8192, np.float32, "flat", 128), (2, 8192, np.float32, "nested", 64),
+    (3, 512, np.float64, "pair", 32), (3, 512, np.float64, "nested", 0),
+    (3, 512, np.float32, "nested", 64), (3, 512, np.float32, "flat", 0),
+]
+
+
+def sample_points(n, ndim, seed=77, count=400):
+    rng = np.random.default_rng(seed)
+    pts = rng.integers(0, n, size=(count, ndim))
+    corners = [[0] * ndim, [n - 1] * ndim, [0, n - 1] + [0] * (ndim - 2), [n - 1, 0] + [n - 1] * (ndim - 2),
+               [1] * ndim, [n - 2] * ndim, [3] * ndim, [n - 4] * ndim, [n // 2] * ndim,
+               [n // 2 - 1] + [0] * (ndim - 1), [0] * (ndim - 1) + [n // 2 - 1], [0] * (ndim - 1) + [n // 2]]
+    pts[:len(corners)] = corners
+    return pts
+
+
+def sampled_reference(x, n, ndim, pts):
+    """Oracle values at the sampled points and the two magnitude sums the
+    tolerances use: sum |c_k x| of the composed weights, and (|B| o |A|)|x|
+    of the factors."""
+    oL = ost.laplacian(ndim, 4)
+    oc = ost.compose(oL, oL)
+    x64 = x.astype(np.float64)
+    w = oracle_weights(oc, Fraction(1, n), np.float64)
+    ref = oap.apply_at(w, x64, "periodic", pts, oc.radius)
+    absw = {k: abs(float(v)) for k, v in w.items()}
+    mag_flat = oap.apply_at(absw, np.abs(x64), "periodic", pts, oc.radius)
+    absL = ost.Stencil.make({k: abs(v) for k, v in oL.coeffs}, oL.hpow)
+    wabs = ost.fp_weights(ost.compose(absL, absL), Fraction(1, n), np.float64)
+    mag_nested = oap.apply_at(wabs, np.abs(x64), "periodic", pts, oc.radius)
+    return ref, mag_flat, mag_nested, oc.npts, oL.npts
+
+
+def schedule_tolerance(how, dt, npts_c, npts_l, mag_flat, mag_nested):
+    """Elementwise bound of each schedule (see the module docstring and the
+    nested and pair tests): flat npts eps sum|w x|; nested (2 n_A + 2) eps
+    (|B| o |A|)|x| (+ npts eps32 for float32 factor weights); pair 2^-42."""
+    eps = np.finfo(dt).eps
+    if how == "flat":
+        return npts_c * eps * mag_flat
+    if how == "pair":
+        return 2.0 ** -42 * mag_nested
+    b = (2 * npts_l + 2) * eps * mag_nested
+    if dt == np.float32:
+        b = b + npts_c * eps * mag_nested
+    return b
+
+
+@pytest.mark.parametrize("ndim,n,dt,how,planes", FULL_SIZE_SCHEDULES)
+def test_full_size_schedules_sampled(ndim, n, dt, how, planes):
+    """The apply-sweep sizes (8192^2, 512^3, periodic, 4th-order Lap o Lap) run
+    through apply_tuned with each evaluation schedule and depth recorded by
+    tune_set -- the path and launch configuration the bench times -- checked on
+    400+ sampled points (corners, the folded-row seam n/2, random) against the
     oracle evaluated point by point."""
     shape = (n,) * ndim
     x = fields.uniform(shape, seed=1234 + ndim, dtype=dt)
-    s = lib_bilap(ndim, 4)
-    os_ = ost.bilaplacian(ndim, 4)
-    w = oracle_weights(os_, Fraction(1, n), dt)
+    L = sc.laplacian(ndim, 4)
     xt = torch.from_numpy(x).to(DEV)
-    yt = torch.empty_like(xt)
-    sc.apply_composed(s, xt, yt, bc="periodic", h=(1, n))
+    yt = torch.full_like(xt, float("nan"))
+    wb = sc.apply_composition_work_bytes(L, L, xt.dtype, "periodic", shape)
+    work = torch.empty(wb, dtype=torch.uint8, device=DEV)
+    sc.tune_set(L, L, xt.dtype, "periodic", shape, {"eval": how, "planes": planes, "ms": 0.0})
+    sc.apply_tuned(L, L, xt, yt, work, h=(1, n))
     torch.cuda.synchronize()
-    rng = np.random.default_rng(77)
-    pts = rng.integers(0, n, size=(400, ndim))
-    pts[:8] = [[0] * ndim, [n - 1] * ndim, [0, n - 1] + [0] * (ndim - 2), [n - 1, 0] + [n - 1] * (ndim - 2),
-               [1] * ndim, [n - 2] * ndim, [3] * ndim, [n - 4] * ndim]
+    del work
+    pts = sample_points(n, ndim)
     y = yt.cpu().numpy()
-    got = np.array([y[tuple(p)] for p in pts], dtype=np.float64)
-    ref = oap.apply_at(w, x, "periodic", pts, os_.radius)
-    absw = {k: abs(float(v)) for k, v in w.items()}
-    mag = oap.apply_at(absw, np.abs(x), "periodic", pts, os_.radius)
-    eps = np.finfo(dt).eps
-    assert np.all(np.abs(got - ref) <= os_.npts * eps * mag)
+    got = y[tuple(pts.T)].astype(np.float64)
+    ref, mag_flat, mag_nested, npts_c, npts_l = sampled_reference(x, n, ndim, pts)
+    tol = schedule_tolerance(how, dt, npts_c, npts_l, mag_flat, mag_nested)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), float(np.max(err / tol))
+    if dt == np.float64:
+        assert np.linalg.norm(err) <= 1e-12 * np.linalg.norm(ref)
+    assert not np.isnan(y).any()
 
 
 def test_invalid_arguments_are_rejected():

@@ -1,10 +1,14 @@
 """GPU solves (plate problem, Cahn-Hilliard steps, batches) against the oracle.
 
-Every solve must reach a TRUE relative residual ||b - A x|| / ||b|| <= rtol
-(recomputed in FP64 by the library).  The error of each result against the
-FP64 oracle solution of the same discrete problem is bounded by
-kappa * (rtol + oracle residual), kappa the closed-form condition number;
-the measured error is printed with each result.
+Every solve must reach a TRUE relative residual ||b - A x|| / ||b|| <= rtol.
+The library reports it (recomputed in FP64 on the device); the tests
+recompute it again with the oracle's own apply, allowing for the rounding of
+either residual computation (npts * eps * || |A| |x| ||).  The error of a
+plate solution against the oracle's sparse direct solution is bounded by
+what that residual implies, ||A^-1 r||, plus the direct solver's own
+rounding (a few kappa eps); Cahn-Hilliard steps (kappa <= 3 at the tested
+sizes) are held to 2 kappa rtol against the DFT closed form.  Measured
+errors are printed with each result.
 """
 from fractions import Fraction
 
@@ -45,6 +49,24 @@ def oracle_bvp(m, n, ndim):
     return obvp.solve_direct(w, m["g"], m["u_padded"], 2)
 
 
+def bvp_residual_and_error_bound(m, n, ndim, xs):
+    """The oracle's true relative residual of xs, the rounding allowance of a
+    residual computed in FP64, and ||A^-1 r|| (the error that residual
+    implies, through the oracle's sparse direct solve)."""
+    import scipy.sparse.linalg as spla
+    B = ost.bilaplacian(ndim, 2)
+    w = ost.fp_weights(B, Fraction(1, n + 1), np.float64)
+    b = obvp.rhs_exact_ghost(w, m["g"], m["u_padded"], 2)
+    r = b - obvp.apply_interior(w, xs, 2)
+    absw = {k: abs(v) for k, v in w.items()}
+    mag = obvp.apply_interior(absw, np.abs(xs), 2)
+    bn = np.linalg.norm(b)
+    A = obvp.assemble_interior(w, b.shape)
+    e_implied = spla.spsolve(A.tocsc(), r.ravel()).reshape(b.shape)
+    return (np.linalg.norm(r) / bn, 2 * B.npts * np.finfo(float).eps * np.linalg.norm(mag) / bn,
+            np.linalg.norm(e_implied))
+
+
 @pytest.mark.parametrize("n,ndim,prec,solver", [
     (16, 2, "f64", "persistent"), (32, 2, "f64", "persistent"), (64, 2, "f64", "persistent"),
     (64, 2, "f64", "plain"), (16, 2, "mixed", "persistent"), (33, 2, "mixed", "persistent"),
@@ -60,13 +82,24 @@ def test_bvp_matches_oracle(n, ndim, prec, solver):
     xs = x.cpu().numpy()
     ref = oracle_bvp(m, n, ndim)
     err = np.linalg.norm(xs - ref) / np.linalg.norm(ref)
+    rel, slack, e_implied = bvp_residual_and_error_bound(m, n, ndim, xs)
+    kap = kappa_bvp(n, ndim)
+    eps = np.finfo(float).eps
     print(f"N={n} {ndim}D {prec} {solver}: iters {info['iters']} outer {info['outer']} "
-          f"relres {info['rel_res']:.2e} err vs oracle {err:.2e}")
-    assert err <= 2 * kappa_bvp(n, ndim) * RTOL
+          f"relres {info['rel_res']:.2e} (oracle {rel:.2e}, rounding {slack:.1e}) err vs oracle {err:.2e} "
+          f"(implied by r {e_implied / np.linalg.norm(ref):.2e}, kappa eps {kap * eps:.1e})")
+    # the residual the library reported, recomputed independently
+    assert rel <= RTOL + slack
+    # the error that residual implies, plus what the residual's own rounding
+    # (npts eps |A||x|, through ||A^-1|| ~ kappa / ||A||) and the direct
+    # solve's rounding (~ kappa eps) can hide
+    bound = 1.1 * e_implied / np.linalg.norm(ref) + 40 * kap * eps
+    assert err <= bound
     # same discretisation error against the exact solution as the oracle
     e_gpu = np.max(np.abs(xs - m["u_exact"]))
     e_ref = np.max(np.abs(ref - m["u_exact"]))
-    assert abs(e_gpu - e_ref) <= 1e-3 * e_ref + 2 * kappa_bvp(n, ndim) * RTOL * np.max(np.abs(ref))
+    assert abs(e_gpu - e_ref) <= np.max(np.abs(xs - ref)) * (1 + 1e-9)
+    assert abs(e_gpu - e_ref) <= 1e-6 * e_ref
 
 
 def test_bvp_second_order_convergence():
@@ -163,6 +196,29 @@ def test_ch_step_matches_oracle(ndim, n, batch, eps, dt, prec):
         assert abs(got[b].sum() - u0[b].sum()) <= 1e-12 * np.abs(u0[b]).sum()
 
 
+def test_ch_3d_batch_of_8_at_256_one_step_matches_oracle():
+    """The 3D Cahn-Hilliard workload at its full size -- 8 seeds of 256^3,
+    eps 0.02, dt 1e-6, 25-point Lap o Lap, one persistent launch, FP32 inner
+    iterations with FP64 refinement -- one step against the DFT closed form
+    for every field, with mass conserved to 1e-12."""
+    n, batch, eps, dt = 256, 8, 0.02, 1e-6
+    u0 = manufactured.ch_uniform(n, 3, seed=2205, amp=0.05, batch=batch)
+    u = torch.from_numpy(u0).to(DEV)
+    c = sc.make_ch((n, n, n), batch, (1, n), dt, 1.0, eps * eps, prec="mixed", rtol=RTOL)
+    infos = sc.ch_step(c, u)
+    got = u.cpu().numpy()
+    del u
+    kap = 1 + dt * eps * eps * (4 * 3 * n * n) ** 2
+    for b in range(batch):
+        assert infos[b]["status"] == 0 and infos[b]["rel_res"] <= RTOL, infos[b]
+        assert infos[b]["prec"] == "mixed"
+        ref = och.step_fft(u0[b], 1.0 / n, dt, 1.0, eps * eps, ("cubic",))
+        err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+        print(f"CH 3D 256^3 b={b}: iters {infos[b]['iters']} relres {infos[b]['rel_res']:.2e} err {err:.2e}")
+        assert err <= 2 * kap * RTOL + 1e-13
+        assert abs(got[b].sum() - u0[b].sum()) <= 1e-12 * np.abs(u0[b]).sum()
+
+
 def test_ch_plain_matches_persistent():
     n = 64
     u0 = manufactured.ch_uniform(n, 2, seed=5, amp=0.3)
@@ -185,6 +241,21 @@ def test_ch_stats_match_oracle():
         assert abs(m[b] - och.mass(u0[b])) <= 1e-12 * np.abs(u0[b]).sum()
         ref = och.free_energy(u0[b], 1.0 / n, 0.02**2, ("cubic",))
         assert abs(e[b] - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("chem", [("cubic",), ("double_well", 5.0, 0.3, 0.7)])
+def test_ch_stats_3d_match_oracle(chem):
+    """Mass and free energy of 3D fields (two batch items, h != 1) against
+    the oracle, for both free energies."""
+    n, L = 40, 3.0
+    u0 = manufactured.ch_uniform(n, 3, seed=9, amp=0.7, batch=2) + (0.5 if chem[0] != "cubic" else 0.0)
+    kw = dict(chem="double_well", rho=5.0, ca=0.3, cb=0.7) if chem[0] != "cubic" else {}
+    c = sc.make_ch((n, n, n), 2, (3, n), 1e-6, 1.0, 0.7, **kw)
+    m, e = sc.ch_stats(c, torch.from_numpy(np.ascontiguousarray(u0)).to(DEV))
+    for b in range(2):
+        assert abs(m[b] - och.mass(u0[b])) <= 1e-12 * np.abs(u0[b]).sum()
+        ref = och.free_energy(u0[b], L / n, 0.7, chem)
+        assert abs(e[b] - ref) <= 1e-12 * abs(ref), (e[b], ref)
 
 
 def test_ch_double_well_matches_oracle():
