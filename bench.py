@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--workload", default="apply_sweep",
                     choices=["apply_sweep", "apply_one", "bvp", "ch2d", "ch3d", "serving"])
     ap.add_argument("--case", default="3d_f64", help="apply_one: {2d,3d}_{f64,f32}")
-    ap.add_argument("--how", default="pair", choices=["flat", "nested", "pair"], help="apply_one evaluation")
+    ap.add_argument("--how", default="pair", choices=["flat", "nested", "pair", "fused"],
+                    help="apply_one evaluation")
+    ap.add_argument("--planes", type=int, default=0, help="apply_one: output planes per CTA (0: model)")
     ap.add_argument("--nreq", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--n2d", default="32,256", help="serving: 2D interior size range (log-uniform)")
     ap.add_argument("--n3d", default="16,40", help="serving: 3D interior size range (log-uniform)")
@@ -236,7 +238,7 @@ def run_apply_sweep_ours(args, rank, world, local):
         ms = statistics.mean(ev[c["name"]])
         per_case[c["name"]] = {"ms": ms, "gbs": c["bytes"] / (ms * 1e-3) / 1e9, "bytes": c["bytes"],
                                "how": c["how"], "tune": tune[c["name"]]}
-        launches += {"flat": 1, "nested": 2, "pair": 4}[c["how"]] * args.steps
+        launches += {"flat": 1, "nested": 2, "pair": 4, "fused": 1}[c["how"]] * args.steps
     step_bytes = sum(c["bytes"] for c in cases)
 
     # end to end through the host-buffer entry point
@@ -265,11 +267,10 @@ def run_apply_one(args, local):
     C = sc.compose_stencil(L, L)
     work = torch.empty(sc.apply_composition_work_bytes(L, L, dt, "periodic", (n,) * nd), dtype=torch.uint8, device=dev)
 
+    sc.tune_set(L, L, dt, "periodic", (n,) * nd, {"eval": args.how, "planes": args.planes})
+
     def go():
-        if args.how == "flat":
-            sc.apply_composed(C, x, y, bc="periodic", h=(1, n))
-        else:
-            sc.apply_composition(L, L, x, y, work=work, bc="periodic", h=(1, n), arith=args.how if args.how == "pair" else "native")
+        sc.apply_tuned(L, L, x, y, work, h=(1, n))
 
     for _ in range(args.warmup):
         go()
@@ -283,7 +284,7 @@ def run_apply_one(args, local):
     ms = a.elapsed_time(b) / args.steps
     nbytes = 2 * n ** nd * x.element_size()
     return {"metric": "composed-stencil apply GB/s (one case)", "value": nbytes / ms / 1e6, "unit": "GB/s",
-            "ms_per_step": ms, "config": {"workload": f"{args.case} n={n} eval={args.how}"}}
+            "ms_per_step": ms, "config": {"workload": f"{args.case} n={n} eval={args.how} planes={args.planes}"}}
 
 
 def run_apply_e2e(sc, cases, dev, stream, args, world):
@@ -696,7 +697,8 @@ def main():
                 "hbm_frac_of_measured": dstat["gbs"] / hbm}
     else:
         kern = {"flat": "flat_apply_kernel", "nested": "flat_apply_kernel x2 (nested B(A x))",
-                "pair": "pk_lap_kernel x2 (FP64 as packed f32x2 pairs, nested B(A x))"}[dstat["how"]]
+                "pair": "pk_lap_kernel x2 (FP64 as packed f32x2 pairs, nested B(A x))",
+                "fused": f"fused{nd}_kernel (nested B(A x) in one pass)"}[dstat["how"]]
         roof = {"bound": "hbm", "achieved": dstat["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": dstat["gbs"] / hbm, "traffic": traffic, "kernel": f"{kern} ({dname})",
                 "peak_source": f"{src} hbm_gbs"}

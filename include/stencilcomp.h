@@ -187,7 +187,12 @@ int sc_apply_composed_host(const sc_stencil *s, int32_t dtype, int32_t bc, const
 typedef enum {
   SC_EVAL_FLAT = 0,   /* sc_apply_composed on compose(outer, inner)           */
   SC_EVAL_NESTED = 1, /* sc_apply_composition, native arithmetic               */
-  SC_EVAL_PAIR = 2    /* sc_apply_composition, FP32-pair arithmetic (FP64)     */
+  SC_EVAL_PAIR = 2,   /* sc_apply_composition, FP32-pair arithmetic (FP64)     */
+  SC_EVAL_FUSED = 3   /* nested B(A x) in one pass, the intermediate kept on
+                         chip (FP32; both factors sums of 1D stencils along the
+                         axes, equal radius 1 or 2; periodic grids of at least
+                         72 x 24 x 8 in 3D and 128 x 8 in 2D); other operators
+                         run SC_EVAL_NESTED                                    */
 } sc_eval;
 
 typedef struct {
@@ -198,7 +203,8 @@ typedef struct {
 } sc_tune_choice;
 
 /* Times every evaluation schedule of the operator compose(outer, inner) --
- * flat composed weights, nested native, nested FP32-pair (FP64 only) --
+ * flat composed weights, nested native, fused nested (FP32, where it
+ * applies), nested FP32-pair (FP64 only) --
  * crossed with several halo-blocking depths (planes per CTA: the occupancy
  * model, 16, 32, 64, 128) on the caller's x/y/work and stream (one warm-up
  * and the median of three runs each; y is overwritten), caches the fastest

@@ -26,6 +26,11 @@ int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int
                         int64_t h_num, int64_t h_den, const void *x, void *y, void *work, cudaStream_t st,
                         int arith, int planes = 0);
 
+// Fused single-pass nested apply (FP32 axis-stencil factors, sc_fused.cu).
+bool fused_supported(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims);
+int fused_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int bc, const int64_t *dims, int64_t hn,
+                  int64_t hd, const void *x, void *y, int planes, cudaStream_t st);
+
 int validate_apply(const sc_stencil *s, int dtype, int bc, const int64_t *dims, int64_t h_num,
                    int64_t h_den);
 // Enqueues y = A x on `st` (no validation of pointers).

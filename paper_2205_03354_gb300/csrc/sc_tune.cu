@@ -53,6 +53,8 @@ static int run_choice(const sc_stencil *B, const sc_stencil *A, const sc_stencil
     ApplyReq q{C, dtype, bc, dims, hn, hd, x, y, nullptr, c.planes};
     return apply_enqueue(q, st);
   }
+  if (c.eval == SC_EVAL_FUSED && fused_supported(B, A, dtype, bc, dims))
+    return fused_enqueue(B, A, dtype, bc, dims, hn, hd, x, y, c.planes, st);
   return composition_enqueue(B, A, dtype, bc, dims, hn, hd, x, y, work, st,
                              c.eval == SC_EVAL_PAIR ? SC_ARITH_PAIR : SC_ARITH_NATIVE, c.planes);
 }
@@ -82,9 +84,10 @@ int sc_autotune_apply(const sc_stencil *outer, const sc_stencil *inner, int32_t 
   const int nd = outer->ndim;
   const int nplanes = int(nd == 3 ? dims[2] : dims[1]);
   std::vector<sc_tune_choice> cands;
-  const int evals[3] = {SC_EVAL_FLAT, SC_EVAL_NESTED, SC_EVAL_PAIR};
+  const int evals[4] = {SC_EVAL_FLAT, SC_EVAL_NESTED, SC_EVAL_PAIR, SC_EVAL_FUSED};
   for (int e : evals) {
     if (e == SC_EVAL_PAIR && dtype != SC_F64) continue;
+    if (e == SC_EVAL_FUSED && !fused_supported(outer, inner, dtype, bc, dims)) continue;
     // planes per CTA: the occupancy model (0) and a spread of fixed depths
     const int ps[5] = {0, 16, 32, 64, 128};
     for (int p : ps) {
@@ -188,7 +191,7 @@ int sc_tune_set(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype,
   if (int rc = validate_apply(outer, dtype, bc, dims, 1, 1)) return rc;
   if (int rc = validate_apply(inner, dtype, bc, dims, 1, 1)) return rc;
   if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
-  if (in->eval < SC_EVAL_FLAT || in->eval > SC_EVAL_PAIR) return fail(SC_EINVAL, "unknown eval %d", in->eval);
+  if (in->eval < SC_EVAL_FLAT || in->eval > SC_EVAL_FUSED) return fail(SC_EINVAL, "unknown eval %d", in->eval);
   if (in->planes < 0 || in->planes > 4096) return fail(SC_EINVAL, "planes %d out of range", in->planes);
   sc_stencil C;
   if (int rc = sc_compose_stencil(outer, inner, &C)) return rc;

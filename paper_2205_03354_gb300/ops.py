@@ -126,7 +126,7 @@ def apply_composition(outer: Stencil, inner: Stencil, x: torch.Tensor, y: torch.
     return y
 
 
-EVAL_NAMES = {0: "flat", 1: "nested", 2: "pair"}
+EVAL_NAMES = {0: "flat", 1: "nested", 2: "pair", 3: "fused"}
 
 
 class TuneChoice(ctypes.Structure):

@@ -123,6 +123,8 @@ FULL_SIZE_SCHEDULES = [
     (2, 8192, np.float32, "flat", 128), (2, 8192, np.float32, "nested", 64),
     (3, 512, np.float64, "pair", 32), (3, 512, np.float64, "nested", 0),
     (3, 512, np.float32, "nested", 64), (3, 512, np.float32, "flat", 0),
+    (3, 512, np.float32, "fused", 0), (3, 512, np.float32, "fused", 32),
+    (2, 8192, np.float32, "fused", 0), (2, 8192, np.float32, "fused", 256),
 ]
 
 
@@ -162,6 +164,7 @@ def schedule_tolerance(how, dt, npts_c, npts_l, mag_flat, mag_nested):
         return npts_c * eps * mag_flat
     if how == "pair":
         return 2.0 ** -42 * mag_nested
+    # nested and fused: the same two FP32 sums per point, in any order
     b = (2 * npts_l + 2) * eps * mag_nested
     if dt == np.float32:
         b = b + npts_c * eps * mag_nested
@@ -196,6 +199,51 @@ def test_full_size_schedules_sampled(ndim, n, dt, how, planes):
     if dt == np.float64:
         assert np.linalg.norm(err) <= 1e-12 * np.linalg.norm(ref)
     assert not np.isnan(y).any()
+
+
+FUSED_CASES = [
+    # ndim, order, dims (x, y[, z]), boundary: several tiles, ragged tails in every axis
+    (3, 4, (136, 40, 21), "periodic"), (3, 2, (72, 24, 8), "periodic"), (3, 4, (72, 24, 8), "periodic"),
+    (3, 4, (67, 19, 23), "zero"), (3, 2, (50, 33, 9), "zero"), (3, 4, (66, 21, 13), "ghosted"),
+    (3, 2, (70, 17, 11), "ghosted"), (3, 4, (9, 5, 4), "zero"),
+    (2, 4, (1100, 301), "periodic"), (2, 2, (128, 8), "periodic"), (2, 4, (1101, 97), "zero"),
+    (2, 2, (250, 33), "ghosted"), (2, 4, (244, 40), "ghosted"), (2, 4, (7, 5), "zero"),
+]
+
+
+@pytest.mark.parametrize("ndim,order,dims,bc", FUSED_CASES)
+def test_fused_nested_matches_oracle(ndim, order, dims, bc):
+    """The single-pass fused nested apply (FP32): the composed operator
+    within the two-pass nested bound for every boundary, with ragged tiles,
+    and not merely the two-pass kernels (its rounding differs from theirs
+    somewhere on a random field)."""
+    L = sc.laplacian(ndim, order)
+    oL = ost.laplacian(ndim, order)
+    oc = ost.compose(oL, oL)
+    R = oc.radius
+    n = dims[0]
+    shape = tuple(reversed(dims))
+    xshape = tuple(v + 2 * R for v in shape) if bc == "ghosted" else shape
+    x = fields.uniform(xshape, seed=zlib.crc32(repr(("fused", ndim, order, dims, bc)).encode()), dtype=np.float32)
+    xt = torch.from_numpy(x).to(DEV)
+    yf = torch.full(shape, float("nan"), dtype=torch.float32, device=DEV)
+    yn = torch.full(shape, float("nan"), dtype=torch.float32, device=DEV)
+    work = torch.empty(sc.apply_composition_work_bytes(L, L, torch.float32, bc, dims), dtype=torch.uint8,
+                       device=DEV)
+    sc.tune_set(L, L, torch.float32, bc, dims, {"eval": "fused", "planes": 0})
+    sc.apply_tuned(L, L, xt, yf, work, bc=bc, h=(1, n), dims=dims)
+    sc.apply_composition(L, L, xt, yn, work, bc=bc, h=(1, n), dims=dims)
+    torch.cuda.synchronize()
+    w = oracle_weights(oc, Fraction(1, n), np.float64)
+    y_ref = oap.apply(w, x.astype(np.float64), bc, R)
+    absL = ost.Stencil.make({k: abs(v) for k, v in oL.coeffs}, oL.hpow)
+    wabs = ost.fp_weights(ost.compose(absL, absL), Fraction(1, n), np.float64)
+    mag = oap.apply(wabs, np.abs(x.astype(np.float64)), bc, R)
+    eps = np.finfo(np.float32).eps
+    bound = (2 * oL.npts + 2 + oc.npts) * eps * mag
+    err = np.abs(yf.cpu().numpy().astype(np.float64) - y_ref)
+    assert np.all(err <= bound), float(np.max(err / (mag + 1e-300)))
+    assert not torch.equal(yf, yn)
 
 
 def test_invalid_arguments_are_rejected():
