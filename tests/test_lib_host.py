@@ -104,7 +104,11 @@ def test_saved_tuning_round_trips_without_a_gpu():
     # another shape stays untuned
     assert lib.sc_tuned_choice(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
                                dims_arg((40, 36, 21)), ctypes.byref(out)) == 1
-    for bad in (TuneChoice(3, 0, 0.0), TuneChoice(0, -1, 0.0), TuneChoice(1, 5000, 0.0)):
+    # the fused schedule is a valid choice (it runs the nested one where it does not apply)
+    ok = TuneChoice(3, 0, 0.0)
+    assert lib.sc_tune_set(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
+                           dims_arg((40, 36, 20)), ctypes.byref(ok)) == 0
+    for bad in (TuneChoice(4, 0, 0.0), TuneChoice(-1, 0, 0.0), TuneChoice(0, -1, 0.0), TuneChoice(1, 5000, 0.0)):
         assert lib.sc_tune_set(ctypes.byref(L), ctypes.byref(L), sc.F64, sc.BC_PERIODIC,
                                dims_arg((40, 36, 20)), ctypes.byref(bad)) == 1
 
