@@ -376,39 +376,60 @@ void sc_noalloc_forget(void);
 int sc_selftest_barrier_timeout(void *work_dev, size_t work_bytes, int64_t spin_limit, int32_t *status_out,
                                 sc_stream_t stream);
 
-/* ---- Serving loop: continuous batching of plate-problem solves ------------- */
+/* ---- Serving loop: continuous batching of plate solves and CH steps -------- */
 
 /* A server owns one scheduler thread on the device that is current when it is
- * created.  Requests are queued by sc_submit and admitted, in arrival order
- * with skipping of requests that do not fit yet, whenever the caller-provided
- * device arena has room for their fields and Krylov state and fewer than
- * max_active requests are resident.  Resident requests advance together in
- * persistent launches of at most slice_ms milliseconds each (every request on
- * its own group of CTAs); between slices finished requests are retired (their
- * solution copied to the caller's host buffer, their memory freed) and newly
- * admitted ones join.  A request's result does not depend on what else is in
- * flight: it is bit-identical to sc_solve_biharmonic with the same precision.
- * The server never allocates device memory: everything lives in the arena. */
+ * created.  Requests -- plate problems (Sec. 3.3) and semi-implicit
+ * Cahn-Hilliard steps (Sec. 4.1, Eq. cahn) of any size -- are queued by
+ * sc_submit and admitted, in arrival order with skipping of requests that do
+ * not fit yet, whenever the caller-provided device arena has room for their
+ * fields and Krylov state and fewer than max_active requests are resident.
+ * Resident requests advance together in persistent launches of at most
+ * slice_ms milliseconds each (every request on its own group of CTAs);
+ * between slices finished requests are retired (their result copied to the
+ * caller's host buffer, their memory freed) and newly admitted ones join.  A
+ * request's result does not depend on what else is in flight: it is
+ * bit-identical to sc_solve_biharmonic / sc_ch_step (batch 1) with the same
+ * precision.  The server never allocates device memory: everything lives in
+ * the arena. */
 typedef struct {
   void *arena_dev;     /* device memory owned by the caller                   */
   size_t arena_bytes;  /* its size: the admission budget                     */
   int32_t max_active;  /* resident requests at most (1..4096)                */
   double slice_ms;     /* length of one persistent launch (> 0)              */
+  int32_t fail_slice;  /* failure-detection test hook, normally 0: with k > 0
+                          the scheduler treats its k-th time slice as failed
+                          (as if the launch had returned an error; nothing is
+                          launched wrongly and the GPU is not involved), so
+                          that the recovery path can be tested             */
 } sc_server_cfg;
 
-/* One plate problem (same meaning as sc_bvp), with HOST buffers: f_host and
- * ghost_host are read at admission, x_host is written when the request
- * completes; all three must stay valid until sc_poll reports it done. */
+typedef enum {
+  SC_REQ_PLATE = 0,  /* plate problem: f_host, ghost_host -> x_host          */
+  SC_REQ_CH = 1      /* one Cahn-Hilliard step of u_host -> x_host           */
+} sc_request_kind;
+
+/* One request with HOST buffers, read at admission (f_host / ghost_host /
+ * u_host) and written when it completes (x_host); all must stay valid until
+ * sc_poll reports it done.  Plate problems: the fields of sc_bvp.  Cahn-
+ * Hilliard steps: the fields of sc_ch with batch 1, u_host the field at step
+ * n (n^ndim values) and x_host receiving the field at step n + 1. */
 typedef struct {
+  int32_t kind;        /* sc_request_kind                                   */
   int32_t ndim;
   int32_t order;
   int64_t n[3];
   int32_t prec;
   double rtol;
   int64_t maxit;
-  const double *f_host;
-  const double *ghost_host;
-  double *x_host;
+  const double *f_host;      /* plate                                       */
+  const double *ghost_host;  /* plate                                       */
+  const double *u_host;      /* Cahn-Hilliard                               */
+  int64_t h_num, h_den;      /* Cahn-Hilliard: spacing                      */
+  double dt, M, kappa;       /* Cahn-Hilliard                               */
+  int32_t chem;              /* Cahn-Hilliard: 0 cubic, 1 double well       */
+  double rho, ca, cb;        /* Cahn-Hilliard: double well                  */
+  double *x_host;            /* result                                      */
 } sc_request;
 
 typedef struct {
@@ -417,7 +438,7 @@ typedef struct {
   int64_t iters;
   double rel_res;    /* true relative residual                              */
   double queue_s;    /* submit -> admission                                 */
-  double latency_s;  /* submit -> solution copied to x_host                 */
+  double latency_s;  /* submit -> result copied to x_host                   */
 } sc_result;
 
 typedef struct sc_server sc_server;
@@ -428,15 +449,22 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out);
 /* Stops the scheduler; requests still queued or resident are abandoned. */
 int sc_server_destroy(sc_server *srv);
 /* Queues a request (never blocks).  SC_EINVAL for a malformed request,
- * SC_ENOMEM if it could never fit in the arena. */
+ * SC_ENOMEM if it could never fit in the arena; once a time slice has
+ * failed, every later submission returns that slice's error. */
 int sc_submit(sc_server *srv, const sc_request *req, uint64_t *ticket);
 /* SC_EPENDING while the request is queued or resident; SC_OK once it is
  * done (x_host written, *out filled; the ticket is then released);
- * SC_EINVAL for an unknown ticket. */
+ * SC_EINVAL for an unknown ticket.  Requests resident when a slice failed
+ * are done with that error as their status (their arena space is freed). */
 int sc_poll(sc_server *srv, uint64_t ticket, sc_result *out);
 /* Waits until nothing is queued or resident, at most timeout_s seconds
  * (SC_ETIMEOUT otherwise). */
 int sc_server_drain(sc_server *srv, double timeout_s);
+/* Snapshot of the scheduler: the error of the first failed slice (SC_OK if
+ * none), free arena bytes (of sc_server's usable arena), requests resident
+ * and queued.  Host-only. */
+int sc_server_status(sc_server *srv, int32_t *worker_error, size_t *free_bytes, size_t *arena_bytes,
+                     int32_t *active, int32_t *pending);
 
 #ifdef __cplusplus
 }

@@ -17,4 +17,4 @@ from .ops import (apply_composed, apply_composed_host, apply_host_work_bytes,  #
                   F64, F32, BC_PERIODIC, BC_GHOSTED, BC_ZERO)
 from .solvers import (solve_biharmonic, solve_biharmonic_batch, make_bvp, bvp_work_bytes,  # noqa: F401
                       make_ch, ch_step, ch_run, ch_stats, ch_work_bytes, SolveInfo, Bvp, Ch)
-from .server import Server, make_request, request_bytes  # noqa: F401
+from .server import Server, make_ch_request, make_request, request_bytes  # noqa: F401

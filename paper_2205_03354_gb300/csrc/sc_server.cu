@@ -1,11 +1,13 @@
-// Serving loop: continuous batching of plate-problem solves on one GPU.
+// Serving loop: continuous batching of plate-problem solves and
+// Cahn-Hilliard steps on one GPU.
 //
 // A scheduler thread alternates between (1) admitting queued requests into
-// free space of the caller's device arena (copy fields in, build b = g -
-// A(ring)), (2) one time slice of the persistent CG engine over every
-// resident request, and (3) retiring converged requests (solution to the
-// caller's host buffer, arena space back to the free list).  Requests that
-// arrive while others run join at the next slice boundary.
+// free space of the caller's device arena (copy fields in, build the
+// right-hand side: b = g - A(ring) for a plate problem, u + dt M Lap f'(u)
+// for a Cahn-Hilliard step), (2) one time slice of the persistent CG engine
+// over every resident request, and (3) retiring converged requests (result
+// to the caller's host buffer, arena space back to the free list).  Requests
+// that arrive while others run join at the next slice boundary.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,6 +69,11 @@ class Arena {
       }
     }
   }
+  size_t free_total() const {
+    size_t m = 0;
+    for (auto &kv : free_) m += kv.second;
+    return m;
+  }
   size_t largest() const {
     size_t m = 0;
     for (auto &kv : free_) m = std::max(m, kv.second);
@@ -84,7 +91,7 @@ struct Req {
   size_t bytes = 0, off = 0;
   SolveProb P;
   ProbAux aux;
-  double *f = nullptr, *g = nullptr, *x = nullptr;
+  double *f = nullptr, *g = nullptr, *x = nullptr;  // x: plate solution or Cahn-Hilliard field
   double t_submit = 0, t_admit = 0, t_done = 0;
   bool done = false;
   sc_result res;
@@ -118,15 +125,51 @@ static sc_bvp as_bvp(const sc_request *r, const double *f, const double *g, doub
   return b;
 }
 
+// Cahn-Hilliard step view of a request (one field, persistent solver).
+static sc_ch as_ch(const sc_request *r) {
+  sc_ch c;
+  std::memset(&c, 0, sizeof(c));
+  c.ndim = r->ndim;
+  c.order = r->order;
+  for (int a = 0; a < 3; ++a) c.n[a] = r->n[a];
+  c.batch = 1;
+  c.h_num = r->h_num;
+  c.h_den = r->h_den;
+  c.dt = r->dt;
+  c.M = r->M;
+  c.kappa = r->kappa;
+  c.chem = r->chem;
+  c.rho = r->rho;
+  c.ca = r->ca;
+  c.cb = r->cb;
+  c.prec = r->prec;
+  c.solver = SC_SOLVER_PERSISTENT;
+  c.rtol = r->rtol;
+  c.maxit = r->maxit;
+  return c;
+}
+
+// The request's spec with device pointers placed at x (f, g for a plate).
+static int request_spec(const sc_request *r, double *f, double *g, double *x, ProbSpec &sp) {
+  if (r->kind == SC_REQ_CH) {
+    sc_ch c = as_ch(r);
+    return ch_single_spec(&c, x, sp);
+  }
+  if (r->kind != SC_REQ_PLATE) return fail(SC_EINVAL, "unknown request kind %d", r->kind);
+  sc_bvp b = as_bvp(r, f, g, x);
+  return bvp_spec(&b, sp);
+}
+
 static int request_layout(const sc_request *r, ProbSpec &sp, size_t *bytes) {
   // validation with placeholder pointers (never dereferenced)
   static double dummy;
-  sc_bvp b = as_bvp(r, &dummy, &dummy, &dummy);
-  if (int rc = bvp_spec(&b, sp)) return rc;
+  if (int rc = request_spec(r, &dummy, &dummy, &dummy, sp)) return rc;
   Carver cv(nullptr, 0);
-  cv.take(npts_of(r) * 8);                 // f
-  cv.take(padded_of(r, sp.R) * 8);         // ghost field
-  cv.take(npts_of(r) * 8);                 // x
+  if (r->kind == SC_REQ_PLATE) {
+    cv.take(npts_of(r) * 8);          // f
+    cv.take(padded_of(r, sp.R) * 8);  // ghost field
+  }
+  cv.take(npts_of(r) * 8);  // x / u
   SolveProb P;
   ProbAux aux;
   layout(sp, cv, P, aux);
@@ -155,6 +198,7 @@ struct sc_server {
   uint64_t next_id = 1;
   bool stop = false;
   int worker_error = 0;
+  long long slices = 0;  // time slices run (the failure hook counts them)
   std::thread worker;
 };
 
@@ -200,17 +244,27 @@ static void worker_loop(sc_server *S) {
     // set up admitted requests (outside the lock)
     for (Req *r : admit) {
       Carver cv(S->arena_base + r->off, r->bytes);
-      const long long n = npts_of(&r->rq), np = padded_of(&r->rq, r->sp.R);
-      r->f = static_cast<double *>(cv.take(n * 8));
-      r->g = static_cast<double *>(cv.take(np * 8));
+      const long long n = npts_of(&r->rq);
+      const bool plate = r->rq.kind == SC_REQ_PLATE;
+      if (plate) {
+        const long long np = padded_of(&r->rq, r->sp.R);
+        r->f = static_cast<double *>(cv.take(n * 8));
+        r->g = static_cast<double *>(cv.take(np * 8));
+        cudaMemcpyAsync(r->f, r->rq.f_host, n * 8, cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(r->g, r->rq.ghost_host, np * 8, cudaMemcpyHostToDevice, S->st);
+      }
       r->x = static_cast<double *>(cv.take(n * 8));
-      cudaMemcpyAsync(r->f, r->rq.f_host, n * 8, cudaMemcpyHostToDevice, S->st);
-      cudaMemcpyAsync(r->g, r->rq.ghost_host, np * 8, cudaMemcpyHostToDevice, S->st);
+      if (!plate) cudaMemcpyAsync(r->x, r->rq.u_host, n * 8, cudaMemcpyHostToDevice, S->st);
       r->sp.x = r->x;
       layout(r->sp, cv, r->P, r->aux);
-      sc_bvp b = as_bvp(&r->rq, r->f, r->g, r->x);
       int rc = upload_prob(r->sp, r->P, r->aux, S->st);
-      if (!rc) rc = setup_bvp(&b, r->sp, r->P, r->aux, S->st);
+      if (!rc && plate) {
+        sc_bvp b = as_bvp(&r->rq, r->f, r->g, r->x);
+        rc = setup_bvp(&b, r->sp, r->P, r->aux, S->st);
+      } else if (!rc) {
+        sc_ch c = as_ch(&r->rq);
+        rc = setup_ch(&c, r->sp, r->P, r->aux, S->st);
+      }
       r->t_admit = now_s();
       std::lock_guard<std::mutex> lk(S->mu);
       if (rc) {
@@ -233,17 +287,28 @@ static void worker_loop(sc_server *S) {
     if (act.empty()) continue;
     std::vector<SolveProb> hp(act.size());
     for (size_t i = 0; i < act.size(); ++i) hp[i] = act[i]->P;
-    int rc = run_persistent(hp, S->dprobs, S->dmap, S->dbars, S->st, LLONG_MAX, S->cfg.slice_ms);
+    ++S->slices;
+    // the test hook stands in for a launch that returned an error: nothing
+    // is launched for that slice
+    int rc = (S->cfg.fail_slice > 0 && S->slices == S->cfg.fail_slice)
+                 ? fail(SC_ECUDA, "time slice %lld failed (injected by the test hook)", S->slices)
+                 : run_persistent(hp, S->dprobs, S->dmap, S->dbars, S->st, LLONG_MAX, S->cfg.slice_ms);
     std::vector<SolveState> hs(act.size());
     if (!rc) rc = gather_states(S->dprobs, int(act.size()), S->dstates, hs.data(), S->st);
     cudaError_t e = cudaStreamSynchronize(S->st);
     if (rc || e != cudaSuccess) {
+      // every resident request ends with the error and gives its arena
+      // space back; later submissions are refused with the same error
       std::lock_guard<std::mutex> lk(S->mu);
-      S->worker_error = rc ? rc : SC_ECUDA;
+      if (!S->worker_error) S->worker_error = rc ? rc : SC_ECUDA;
+      const double t = now_s();
       for (Req *r : act) {
         std::memset(&r->res, 0, sizeof(r->res));
         r->res.status = S->worker_error;
+        r->res.queue_s = r->t_admit - r->t_submit;
+        r->res.latency_s = t - r->t_submit;
         r->done = true;
+        S->arena.release(r->off, r->bytes);
       }
       S->active.clear();
       S->cv_done.notify_all();
@@ -285,6 +350,7 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
   if (!cfg || !out || !cfg->arena_dev) return fail(SC_EINVAL, "null argument");
   if (cfg->max_active < 1 || cfg->max_active > 4096) return fail(SC_EINVAL, "max_active must be 1..4096");
   if (!(cfg->slice_ms > 0.0)) return fail(SC_EINVAL, "slice_ms must be positive");
+  if (cfg->fail_slice < 0) return fail(SC_EINVAL, "fail_slice must be >= 0");
   // the CTA -> problem map must hold the largest grid any persistent-kernel
   // variant can launch: bound it by the hardware limit of resident CTAs
   const int G = 32 * num_sms();
@@ -334,7 +400,13 @@ int sc_server_destroy(sc_server *S) {
 
 int sc_submit(sc_server *S, const sc_request *req, uint64_t *ticket) {
   if (!S || !req || !ticket) return fail(SC_EINVAL, "null argument");
-  if (!req->f_host || !req->ghost_host || !req->x_host) return fail(SC_EINVAL, "null host buffer");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->worker_error) return fail(S->worker_error, "the server stopped after a failed time slice");
+  }
+  if (!req->x_host) return fail(SC_EINVAL, "null host buffer");
+  if (req->kind == SC_REQ_PLATE && (!req->f_host || !req->ghost_host)) return fail(SC_EINVAL, "null host buffer");
+  if (req->kind == SC_REQ_CH && !req->u_host) return fail(SC_EINVAL, "null host buffer");
   Req *r = new Req();
   r->rq = *req;
   if (int rc = request_layout(req, r->sp, &r->bytes)) {
@@ -368,6 +440,19 @@ int sc_poll(sc_server *S, uint64_t ticket, sc_result *out) {
   *out = r->res;
   delete r;
   S->all.erase(it);
+  clear_error();
+  return SC_OK;
+}
+
+int sc_server_status(sc_server *S, int32_t *worker_error, size_t *free_bytes, size_t *arena_bytes,
+                     int32_t *active, int32_t *pending) {
+  if (!S) return fail(SC_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (worker_error) *worker_error = S->worker_error;
+  if (free_bytes) *free_bytes = S->arena.free_total();
+  if (arena_bytes) *arena_bytes = S->arena_size;
+  if (active) *active = int32_t(S->active.size());
+  if (pending) *pending = int32_t(S->pending.size());
   clear_error();
   return SC_OK;
 }

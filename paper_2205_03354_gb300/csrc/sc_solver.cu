@@ -327,7 +327,7 @@ int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux 
 }
 
 // Right-hand side of a Cahn-Hilliard step: rhs = u + dt M Lap(f'(u)).
-static int setup_ch(const sc_ch *cp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
+int setup_ch(const sc_ch *cp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st) {
   k_fprime<<<grid1d(P.npts), 256, 0, st>>>(P.x, aux.scratch, P.npts, cp->chem, cp->rho, cp->ca, cp->cb);
   sc_stencil L;
   sc_laplacian(sp.ndim, sp.order, &L);
@@ -682,6 +682,12 @@ static int ch_validate(const sc_ch *c) {
   if (c->solver != SC_SOLVER_PERSISTENT && c->solver != SC_SOLVER_PLAIN) return fail(SC_EINVAL, "bad solver");
   if (c->prec < 0 || c->prec > 2) return fail(SC_EINVAL, "bad prec");
   return SC_OK;
+}
+
+int ch_single_spec(const sc_ch *c, double *u, ProbSpec &sp) {
+  if (int rc = ch_validate(c)) return rc;
+  if (c->batch != 1) return fail(SC_EINVAL, "a served Cahn-Hilliard request holds one field");
+  return ch_spec(c, 0, u, sp);
 }
 
 // Work space of a set of problems: per-problem areas + batch descriptors.

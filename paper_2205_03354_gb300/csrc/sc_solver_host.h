@@ -54,6 +54,11 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux);
 int upload_prob(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
 // Right-hand side b = g - A(ring) and x = 0 of a plate problem (enqueued).
 int setup_bvp(const sc_bvp *bp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
+// Right-hand side u + dt M Lap f'(u) of a Cahn-Hilliard step; x (= u, the
+// initial guess) in place (enqueued).
+int setup_ch(const sc_ch *cp, const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st);
+// Validated spec of a one-field Cahn-Hilliard step on the device field u.
+int ch_single_spec(const sc_ch *c, double *u, ProbSpec &sp);
 struct SolveState;
 // Copies the solver states of the n problems described at dprobs to host
 // (one gather kernel into dout, one copy; synchronous).

@@ -1,5 +1,5 @@
 """Serving loop binding (marshalling only): sc_server_create / sc_submit /
-sc_poll / sc_server_drain / sc_server_destroy."""
+sc_poll / sc_server_drain / sc_server_status / sc_server_destroy."""
 from __future__ import annotations
 
 import ctypes
@@ -13,15 +13,22 @@ from .solvers import _PREC
 EPENDING = 9
 
 
+REQ_PLATE, REQ_CH = 0, 1
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("arena_dev", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
-                ("max_active", ctypes.c_int32), ("slice_ms", ctypes.c_double)]
+                ("max_active", ctypes.c_int32), ("slice_ms", ctypes.c_double), ("fail_slice", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("ndim", ctypes.c_int32), ("order", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
-                ("prec", ctypes.c_int32), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int64),
-                ("f_host", ctypes.c_void_p), ("ghost_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p)]
+    _fields_ = [("kind", ctypes.c_int32), ("ndim", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 3), ("prec", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int64), ("f_host", ctypes.c_void_p), ("ghost_host", ctypes.c_void_p),
+                ("u_host", ctypes.c_void_p), ("h_num", ctypes.c_int64), ("h_den", ctypes.c_int64),
+                ("dt", ctypes.c_double), ("M", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("chem", ctypes.c_int32), ("rho", ctypes.c_double), ("ca", ctypes.c_double),
+                ("cb", ctypes.c_double), ("x_host", ctypes.c_void_p)]
 
 
 class Result(ctypes.Structure):
@@ -46,14 +53,24 @@ lib.sc_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)
 lib.sc_poll.restype = ctypes.c_int
 lib.sc_server_drain.argtypes = [ctypes.c_void_p, ctypes.c_double]
 lib.sc_server_drain.restype = ctypes.c_int
+lib.sc_server_status.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t),
+                                 ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_int32)]
+lib.sc_server_status.restype = ctypes.c_int
+
+
+def _host_f64(*arrays):
+    for a in arrays:
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous float64 arrays")
 
 
 def make_request(f: np.ndarray, ghost: np.ndarray, x: np.ndarray, order=2, prec="auto", rtol=1e-10,
                  maxit=10_000_000) -> Request:
-    for a in (f, ghost, x):
-        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-            raise ValueError("host buffers must be C-contiguous float64 arrays")
+    """A plate problem (Sec. 3.3): f and the ghosted exact field in, x out."""
+    _host_f64(f, ghost, x)
     r = Request()
+    r.kind = REQ_PLATE
     r.ndim, r.order = x.ndim, order
     for a, s in enumerate(reversed(x.shape)):
         r.n[a] = s
@@ -63,29 +80,68 @@ def make_request(f: np.ndarray, ghost: np.ndarray, x: np.ndarray, order=2, prec=
     return r
 
 
+def make_ch_request(u: np.ndarray, x: np.ndarray, h, dt, M=1.0, kappa=1e-4, chem="cubic", rho=0.0, ca=0.0,
+                    cb=0.0, order=2, prec="auto", rtol=1e-10, maxit=1_000_000) -> Request:
+    """One semi-implicit Cahn-Hilliard step (Sec. 4.1) of the field u into x."""
+    _host_f64(u, x)
+    if u.shape != x.shape:
+        raise ValueError("u and x must have the same shape")
+    r = Request()
+    r.kind = REQ_CH
+    r.ndim, r.order = x.ndim, order
+    for a, s in enumerate(reversed(x.shape)):
+        r.n[a] = s
+    r.prec = _PREC[prec] if isinstance(prec, str) else int(prec)
+    r.rtol, r.maxit = rtol, maxit
+    r.u_host, r.x_host = u.ctypes.data, x.ctypes.data
+    r.h_num, r.h_den = int(h[0]), int(h[1])
+    r.dt, r.M, r.kappa = dt, M, kappa
+    r.chem = 0 if chem == "cubic" else 1
+    r.rho, r.ca, r.cb = rho, ca, cb
+    return r
+
+
 def request_bytes(r: Request) -> int:
     return int(lib.sc_request_bytes(ctypes.byref(r)))
 
 
 class Server:
-    """Continuous-batching plate-problem server on the current device."""
+    """Continuous-batching server of plate problems and Cahn-Hilliard steps on
+    the current device."""
 
-    def __init__(self, arena: torch.Tensor, max_active: int = 256, slice_ms: float = 2.0):
+    def __init__(self, arena: torch.Tensor, max_active: int = 256, slice_ms: float = 2.0, fail_slice: int = 0):
         if not arena.is_cuda:
             raise ValueError("arena must be a CUDA tensor")
         self._arena = arena
-        cfg = ServerCfg(arena.data_ptr(), arena.numel() * arena.element_size(), max_active, slice_ms)
+        cfg = ServerCfg(arena.data_ptr(), arena.numel() * arena.element_size(), max_active, slice_ms, fail_slice)
         h = ctypes.c_void_p()
         check(lib.sc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self._keep = {}
 
     def submit(self, f, ghost, x, **kw) -> int:
+        """Queues a plate problem; returns its ticket."""
         r = make_request(f, ghost, x, **kw)
         t = ctypes.c_uint64()
         check(lib.sc_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (f, ghost, x)
         return t.value
+
+    def submit_ch(self, u, x, h, dt, **kw) -> int:
+        """Queues one Cahn-Hilliard step of u (result into x); returns its ticket."""
+        r = make_ch_request(u, x, h, dt, **kw)
+        t = ctypes.c_uint64()
+        check(lib.sc_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (u, x)
+        return t.value
+
+    def status(self) -> dict:
+        err, act, pend = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        free, tot = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib.sc_server_status(self._h, ctypes.byref(err), ctypes.byref(free), ctypes.byref(tot),
+                                   ctypes.byref(act), ctypes.byref(pend)))
+        return {"worker_error": int(err.value), "free_bytes": int(free.value), "arena_bytes": int(tot.value),
+                "active": int(act.value), "pending": int(pend.value)}
 
     def poll(self, ticket: int):
         res = Result()

@@ -120,3 +120,89 @@ def test_burst_of_many_requests_all_converge():
             assert np.array_equal(solo, x)
     finally:
         srv.close()
+
+
+def _ch_solo(u0, n, ndim, h, dt, kappa, prec, chem_kw):
+    u = torch.from_numpy(u0.copy()).to(DEV).reshape((1,) + u0.shape)
+    c = sc.make_ch((n,) * ndim, 1, h, dt, 1.0, kappa, prec=prec, rtol=1e-10, **chem_kw)
+    info = sc.ch_step(c, u)[0]
+    return u[0].cpu().numpy(), info
+
+
+def test_plate_and_cahn_hilliard_requests_same_alone_and_in_the_mix():
+    """Plate problems and Cahn-Hilliard steps (2D and 3D, cubic and double
+    well, FP64 and mixed precision) of several sizes served together: every
+    result is bit-identical to the same request solved alone (sc_ch_step
+    with batch 1 / sc_solve_biharmonic), and the Cahn-Hilliard steps match
+    the oracle's DFT closed form."""
+    from oracle import ch as och
+    arena = torch.empty(1 << 30, dtype=torch.uint8, device=DEV)
+    srv = sc.Server(arena, max_active=64, slice_ms=1.0)
+    ch_specs = [(64, 2, (1, 64), 2e-5, 0.05 ** 2, "auto", {}), (96, 2, (1, 96), 1e-6, 0.01 ** 2, "mixed", {}),
+                (24, 3, (1, 24), 1e-5, 0.05 ** 2, "f64", {}),
+                (48, 2, (200, 48), 0.05, 2.0, "auto", dict(chem="double_well", rho=5.0, ca=0.3, cb=0.7))]
+    try:
+        jobs = []
+        for k, (n, nd, ks) in enumerate(SPECS[:5]):
+            f, g = _case(n, nd, ks)
+            x = np.full(f.shape, np.nan)
+            jobs.append(("plate", srv.submit(f, g, x, prec="auto"), (f, g), x))
+            if k < len(ch_specs):
+                cn, cnd, h, dt, kap, prec, kw = ch_specs[k]
+                u0 = manufactured.ch_uniform(cn, cnd, seed=50 + k, amp=0.3) + (0.5 if kw else 0.0)
+                u0 = np.ascontiguousarray(u0)
+                xc = np.full(u0.shape, np.nan)
+                jobs.append(("ch", srv.submit_ch(u0, xc, h, dt, kappa=kap, prec=prec, **kw),
+                             (u0, cn, cnd, h, dt, kap, prec, kw), xc))
+        srv.drain(300.0)
+        for kind, t, args, x in jobs:
+            res = srv.poll(t)
+            assert res is not None and res["status"] == 0 and res["rel_res"] <= 1e-10, (kind, res)
+            if kind == "plate":
+                solo, info = _solo(*args, res["prec"])
+            else:
+                u0, cn, cnd, h, dt, kap, prec, kw = args
+                solo, info = _ch_solo(u0, cn, cnd, h, dt, kap, res["prec"], kw)
+                chem = ("double_well", 5.0, 0.3, 0.7) if kw else ("cubic",)
+                ref = och.step_fft(u0, h[0] / h[1], dt, 1.0, kap, chem)
+                assert np.max(np.abs(x - ref)) <= 1e-8 * max(1.0, np.max(np.abs(ref)))
+            assert info["iters"] == res["iters"], kind
+            assert np.array_equal(solo, x), kind
+    finally:
+        srv.close()
+
+
+def test_failed_time_slice_frees_the_arena_and_refuses_new_work():
+    """Failure detection without a GPU fault: the scheduler's test hook makes
+    its second time slice fail as a failed launch would.  The requests then
+    resident end with SC_ECUDA, their arena space comes back (free bytes equal
+    the arena again), later submissions are refused with the same error, and
+    the device keeps working."""
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device=DEV)
+    srv = sc.Server(arena, max_active=16, slice_ms=0.2, fail_slice=2)
+    try:
+        jobs = []
+        for n, nd, ks in SPECS:
+            f, g = _case(n, nd, ks)
+            x = np.full(f.shape, np.nan)
+            try:
+                jobs.append(srv.submit(f, g, x, prec="f64"))
+            except sc.ScError as e:  # the failure may already have happened
+                assert e.status == 7 and jobs
+        srv.drain(120.0)
+        res = [srv.poll(t) for t in jobs]
+        assert all(r is not None for r in res)
+        assert any(r["status"] == 7 for r in res)  # SC_ECUDA for those resident at the failure
+        assert all(r["status"] in (0, 7) for r in res)
+        st = srv.status()
+        assert st["worker_error"] == 7 and st["active"] == 0 and st["pending"] == 0
+        assert st["free_bytes"] == st["arena_bytes"]
+        f, g = _case(16, 2, (1, 1))
+        with pytest.raises(sc.ScError) as e:
+            srv.submit(f, g, np.empty_like(f))
+        assert e.value.status == 7
+    finally:
+        srv.close()
+    f, g = _case(16, 2, (1, 1))
+    solo, info = _solo(f, g, "f64")
+    assert info["status"] == 0 and info["rel_res"] <= 1e-10
