@@ -222,6 +222,22 @@ int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dty
 /* The cached choice for a shape (SC_EINVAL if not tuned). */
 int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
                     const int64_t *dims, sc_tune_choice *out);
+/* The tuned apply (as sc_apply_tuned) with x and y in HOST memory, for data
+ * that lives on the host: x is copied into the device work space on a
+ * library copy-in stream, the tuned schedule runs on `stream`, y is copied
+ * back on a library copy-out stream, and `stream` is made to wait for that
+ * copy.  Asynchronous: synchronise `stream` before reading y_host.  Pinned
+ * host buffers let the copies run at link speed.  Consecutive calls on one
+ * device overlap: the next call's copy-in (which waits only until the
+ * previous apply has read its input) runs while the previous result is
+ * copied out.  work_bytes >= sc_apply_tuned_host_work_bytes(...); one work
+ * space may serve consecutive calls.  Calls from several host threads are
+ * serialised by the library. */
+size_t sc_apply_tuned_host_work_bytes(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype,
+                                      int32_t bc, const int64_t *dims);
+int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                        const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_host, void *y_host,
+                        void *work_dev, size_t work_bytes, sc_stream_t stream);
 /* Records a choice for a shape in the process cache without timing, e.g. one
  * saved from an earlier sc_autotune_apply run, so that sc_apply_tuned reuses
  * it (a later sc_autotune_apply for the shape replaces it).  eval is an

@@ -174,6 +174,79 @@ int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dty
   return rc;
 }
 
+size_t sc_apply_tuned_host_work_bytes(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype,
+                                      int32_t bc, const int64_t *dims) {
+  if (!outer || !inner || !dims) return 0;
+  if (validate_apply(outer, dtype, bc, dims, 1, 1) || validate_apply(inner, dtype, bc, dims, 1, 1)) return 0;
+  if (outer->ndim != inner->ndim) return 0;
+  const size_t es = dtype == SC_F64 ? 8 : 4;
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const int nd = outer->ndim, rin = bc == SC_BC_GHOSTED ? outer->radius + inner->radius : 0;
+  return up(grid_elems_ext(nd, dims, rin) * es) + up(grid_elems_ext(nd, dims, 0) * es) +
+         composition_work_bytes(outer, inner, dtype, bc, dims);
+}
+
+// Per-device copy streams and the events that order consecutive host-buffer
+// applies (created on first use, kept until exit).
+struct HostPipe {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t in_done = nullptr, comp_done = nullptr, out_done = nullptr;
+  bool primed = false;  // comp_done / out_done recorded at least once
+};
+static std::mutex g_pipe_mu;
+static HostPipe g_pipe[64];
+
+int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
+                        const int64_t *dims, int64_t h_num, int64_t h_den, const void *x_host, void *y_host,
+                        void *work_dev, size_t work_bytes, sc_stream_t stream) {
+  if (int rc = validate_apply(outer, dtype, bc, dims, h_num, h_den)) return rc;
+  if (int rc = validate_apply(inner, dtype, bc, dims, h_num, h_den)) return rc;
+  if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
+  if (!x_host || !y_host || !work_dev) return fail(SC_EINVAL, "null pointer");
+  const size_t need = sc_apply_tuned_host_work_bytes(outer, inner, dtype, bc, dims);
+  if (work_bytes < need) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, need);
+  const size_t es = dtype == SC_F64 ? 8 : 4;
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const int nd = outer->ndim, rin = bc == SC_BC_GHOSTED ? outer->radius + inner->radius : 0;
+  const size_t xb = grid_elems_ext(nd, dims, rin) * es, yb = grid_elems_ext(nd, dims, 0) * es;
+  char *xd = static_cast<char *>(work_dev), *yd = xd + up(xb), *wd = yd + up(yb);
+  const size_t wb = work_bytes - up(xb) - up(yb);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe &hp = g_pipe[dev & 63];
+  if (!hp.in) {
+    if (cudaStreamCreateWithFlags(&hp.in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&hp.out, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&hp.in_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&hp.comp_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&hp.out_done, cudaEventDisableTiming) != cudaSuccess)
+      return fail(SC_ECUDA, "copy stream or event creation failed");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // copy-in: after the previous apply has read the previous input
+  if (hp.primed) cudaStreamWaitEvent(hp.in, hp.comp_done, 0);
+  if (cudaMemcpyAsync(xd, x_host, xb, cudaMemcpyHostToDevice, hp.in) != cudaSuccess)
+    return fail(SC_ECUDA, "host-to-device copy failed");
+  cudaEventRecord(hp.in_done, hp.in);
+  // apply: after the copy-in, and after the previous result has left yd
+  cudaStreamWaitEvent(st, hp.in_done, 0);
+  if (hp.primed) cudaStreamWaitEvent(st, hp.out_done, 0);
+  if (int rc = sc_apply_tuned(outer, inner, dtype, bc, dims, h_num, h_den, xd, yd, wd, wb, stream)) return rc;
+  cudaEventRecord(hp.comp_done, st);
+  // copy-out, and the caller's stream waits for it
+  cudaStreamWaitEvent(hp.out, hp.comp_done, 0);
+  if (cudaMemcpyAsync(y_host, yd, yb, cudaMemcpyDeviceToHost, hp.out) != cudaSuccess)
+    return fail(SC_ECUDA, "device-to-host copy failed");
+  cudaEventRecord(hp.out_done, hp.out);
+  cudaStreamWaitEvent(st, hp.out_done, 0);
+  hp.primed = true;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SC_ECUDA, "host apply: %s", cudaGetErrorString(e));
+  clear_error();
+  return SC_OK;
+}
+
 int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
                     const int64_t *dims, sc_tune_choice *out) {
   if (!outer || !inner || !dims || !out) return fail(SC_EINVAL, "null argument");

@@ -175,6 +175,35 @@ def apply_tuned(outer: Stencil, inner: Stencil, x, y, work, bc="periodic", h=(1,
     return y
 
 
+lib.sc_apply_tuned_host_work_bytes.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _I64P]
+lib.sc_apply_tuned_host_work_bytes.restype = ctypes.c_size_t
+lib.sc_apply_tuned_host.argtypes = _TUNE_ARGS + [ctypes.c_void_p]
+lib.sc_apply_tuned_host.restype = ctypes.c_int
+
+
+def apply_tuned_host_work_bytes(outer: Stencil, inner: Stencil, dtype, bc, dims) -> int:
+    return int(lib.sc_apply_tuned_host_work_bytes(ctypes.byref(outer), ctypes.byref(inner), dtype_code(dtype),
+                                                  bc_code(bc), dims_arg(dims)))
+
+
+def apply_tuned_host(outer: Stencil, inner: Stencil, x, y, work, bc="periodic", h=(1, 1), dims=None, stream=None):
+    """The tuned apply with x and y in host memory (pinned for link-speed
+    copies).  Asynchronous: synchronise the stream before reading y."""
+    for name, t in (("x", x), ("y", y)):
+        if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    if y.dtype != x.dtype:
+        raise TypeError("x and y must have the same dtype")
+    require_device("work", work)
+    if dims is None:
+        dims = tuple(reversed(y.shape))
+    check(lib.sc_apply_tuned_host(ctypes.byref(outer), ctypes.byref(inner), dtype_code(y.dtype), bc_code(bc),
+                                  dims_arg(dims), int(h[0]), int(h[1]), ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                  work.numel() * work.element_size(), stream_arg(stream)))
+    return y
+
+
 def tune_set(outer: Stencil, inner: Stencil, dtype, bc, dims, choice: dict) -> None:
     """Records a saved tuning choice ({"eval", "planes", "ms"}) for a shape so
     that apply_tuned reuses it without timing."""
