@@ -260,7 +260,12 @@ typedef enum {
 
 typedef enum {
   SC_SOLVER_PERSISTENT = 0, /* one cooperative launch runs the whole CG loop  */
-  SC_SOLVER_PLAIN = 1       /* one kernel per CG operation, host-driven loop  */
+  SC_SOLVER_PLAIN = 1,      /* one kernel per CG operation, host-driven loop  */
+  SC_SOLVER_PCG = 2         /* plate problems only: host-driven FP64 CG
+                               preconditioned by the inverse of L_D^2 (L_D the
+                               Dirichlet Laplacian) applied with sine transforms
+                               in FP32; tens of iterations where plain CG needs
+                               O(N^2) (large grids)                              */
 } sc_solver_kind;
 
 typedef struct {

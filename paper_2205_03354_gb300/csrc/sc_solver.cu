@@ -260,6 +260,23 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
   long long padded = 1;
   for (int a = 0; a < sp.ndim; ++a) padded *= sp.n[a] + 2 * sp.R;
   aux.scratch = static_cast<double *>(cv.take(std::max<long long>(padded, npts) * 8));
+  if (sp.solver == SC_SOLVER_PCG) {
+    const long long N = sp.n[0];
+    aux.z = static_cast<double *>(cv.take(npts * 8));
+    aux.u0 = static_cast<float *>(cv.take(npts * 4));
+    aux.u1 = static_cast<float *>(cv.take(npts * 4));
+    aux.S = static_cast<float *>(cv.take(N * N * 4));
+    aux.lam1 = static_cast<double *>(cv.take(N * 8));
+    aux.part = static_cast<double *>(cv.take(3 * pcg_parts(npts) * 8));
+    aux.out = static_cast<double *>(cv.take(8 * 8));
+    const long long K0 = pcg_low_modes(sp.ndim, N);
+    aux.Sl = static_cast<double *>(cv.take(K0 * N * 8));
+    aux.SlT = static_cast<double *>(cv.take(K0 * N * 8));
+    aux.wa = static_cast<double *>(cv.take((sp.ndim == 3 ? N * N : N) * K0 * 8));
+    aux.wb = static_cast<double *>(cv.take(N * K0 * K0 * 8));
+    aux.wc = static_cast<double *>(cv.take(K0 * K0 * K0 * 8));
+    aux.zl = static_cast<double *>(cv.take(npts * 8));
+  }
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -622,7 +639,8 @@ int bvp_spec(const sc_bvp *b, ProbSpec &sp) {
   for (int a = 0; a < b->ndim; ++a)
     if (b->n[a] != b->n[0] || b->n[a] < 1 || b->n[a] > 65536) return fail(SC_EINVAL, "n must be equal per axis, 1..65536");
   if (!(b->rtol > 0.0) || b->maxit < 0) return fail(SC_EINVAL, "bad rtol/maxit");
-  if (b->solver != SC_SOLVER_PERSISTENT && b->solver != SC_SOLVER_PLAIN) return fail(SC_EINVAL, "bad solver");
+  if (b->solver != SC_SOLVER_PERSISTENT && b->solver != SC_SOLVER_PLAIN && b->solver != SC_SOLVER_PCG)
+    return fail(SC_EINVAL, "bad solver");
   if (b->prec < 0 || b->prec > 2) return fail(SC_EINVAL, "bad prec");
   if (!b->f_dev || !b->ghost_dev || !b->x_dev) return fail(SC_EINVAL, "null device pointer");
   std::memset(&sp, 0, sizeof(sp));
@@ -740,6 +758,8 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
     if (sps[i].solver == SC_SOLVER_PLAIN) {
       k_fill<<<grid1d(hp[i].npts), 256, 0, st>>>(aux[i].ones, 1.0, hp[i].npts);
       if (int rc = run_plain(sps[i], hp[i], aux[i], st, &plain_res[3 * i])) return rc;
+    } else if (sps[i].solver == SC_SOLVER_PCG) {
+      if (int rc = run_pcg(sps[i], hp[i], aux[i], st, &plain_res[3 * i])) return rc;
     } else {
       any_persistent = true;
     }
@@ -748,7 +768,7 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
     std::vector<SolveProb> sub;
     std::vector<int> back;
     for (size_t i = 0; i < sps.size(); ++i)
-      if (sps[i].solver != SC_SOLVER_PLAIN) {
+      if (sps[i].solver == SC_SOLVER_PERSISTENT) {
         sub.push_back(hp[i]);
         back.push_back(int(i));
       }
@@ -757,7 +777,7 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
   }
   std::vector<SolveState> hs(sps.size());
   for (size_t i = 0; i < sps.size(); ++i)
-    if (sps[i].solver != SC_SOLVER_PLAIN)
+    if (sps[i].solver == SC_SOLVER_PERSISTENT)
       cudaMemcpyAsync(&hs[i], hp[i].st, sizeof(SolveState), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(SC_ECUDA, "solve: %s", cudaGetErrorString(e));
@@ -767,7 +787,7 @@ int solve_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, sc_solv
     std::memset(&in, 0, sizeof(in));
     in.prec = sps[i].mixed ? SC_PREC_MIXED : SC_PREC_F64;
     in.seconds = sec;
-    if (sps[i].solver == SC_SOLVER_PLAIN) {
+    if (sps[i].solver != SC_SOLVER_PERSISTENT) {
       in.iters = (long long)plain_res[3 * i];
       in.rel_res = plain_res[3 * i + 1];
       in.status = int(plain_res[3 * i + 2]);

@@ -28,7 +28,26 @@ struct ProbAux {
   int nbox;
   double *scratch;  // set-up scratch (padded grid)
   double *ones;     // vector of ones (plain mean fix)
+  // preconditioned solver (SC_SOLVER_PCG) only
+  double *z = nullptr;             // preconditioned residual (FP64)
+  float *u0 = nullptr, *u1 = nullptr;  // FP32 transform buffers
+  float *S = nullptr;              // DST-I matrix, N x N
+  double *lam1 = nullptr;          // 1D Dirichlet eigenvalues, N
+  double *part = nullptr, *out = nullptr;  // dot-product partials and results
+  // the lowest K0^ndim modes in FP64: their rows of the transform (K0 x N
+  // and its transpose), transform work space and the FP64 result
+  double *Sl = nullptr, *SlT = nullptr, *wa = nullptr, *wb = nullptr, *wc = nullptr, *zl = nullptr;
 };
+
+// Low-mode block edge of the preconditioner (modes with every index < K0
+// are transformed in FP64).
+int pcg_low_modes(int ndim, long long N);
+
+// Preconditioned plate solve (sc_pcg.cu): res[0] iterations, res[1] true
+// relative residual, res[2] status.  Synchronous.
+int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st, double *res);
+// Dot-product partial slots the preconditioned solver needs for n points.
+long long pcg_parts(long long n);
 
 // Sub-allocates 256-byte aligned pieces of a caller buffer (base == nullptr:
 // sizing only).

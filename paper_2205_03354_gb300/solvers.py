@@ -10,9 +10,9 @@ from ._lib_loader import check, lib
 from .ops import require_device, stream_arg
 
 PREC_F64, PREC_MIXED, PREC_AUTO = 0, 1, 2
-SOLVER_PERSISTENT, SOLVER_PLAIN = 0, 1
+SOLVER_PERSISTENT, SOLVER_PLAIN, SOLVER_PCG = 0, 1, 2
 _PREC = {"f64": PREC_F64, "mixed": PREC_MIXED, "auto": PREC_AUTO}
-_SOLVER = {"persistent": SOLVER_PERSISTENT, "plain": SOLVER_PLAIN}
+_SOLVER = {"persistent": SOLVER_PERSISTENT, "plain": SOLVER_PLAIN, "pcg": SOLVER_PCG}
 
 
 class SolveInfo(ctypes.Structure):

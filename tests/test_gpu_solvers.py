@@ -102,6 +102,50 @@ def test_bvp_matches_oracle(n, ndim, prec, solver):
     assert abs(e_gpu - e_ref) <= 1e-6 * e_ref
 
 
+@pytest.mark.parametrize("n,ndim", [(64, 2), (200, 2), (300, 2), (20, 3), (28, 3)])
+def test_bvp_pcg_matches_oracle(n, ndim):
+    """The sine-transform-preconditioned solver: the same discrete plate
+    problem as the other solvers, to a true relative residual of 1e-10
+    (recomputed by the oracle), within the error that residual implies of the
+    oracle's direct solution, in tens of iterations."""
+    m, f, g, x = bvp_inputs(n, ndim, ks=(1, 2, 1)[:ndim])
+    info = sc.solve_biharmonic(f, g, x, solver="pcg", rtol=RTOL)
+    assert info["status"] == 0 and info["rel_res"] <= RTOL, info
+    assert info["iters"] <= 60, info
+    xs = x.cpu().numpy()
+    rel, slack, e_implied = bvp_residual_and_error_bound(m, n, ndim, xs)
+    assert rel <= RTOL + slack
+    ref = oracle_bvp(m, n, ndim)
+    err = np.linalg.norm(xs - ref) / np.linalg.norm(ref)
+    eps = np.finfo(float).eps
+    print(f"PCG N={n} {ndim}D: iters {info['iters']} relres {info['rel_res']:.2e} (oracle {rel:.2e}) "
+          f"err vs oracle {err:.2e}")
+    assert err <= 1.1 * e_implied / np.linalg.norm(ref) + 40 * kappa_bvp(n, ndim) * eps
+
+
+def test_bvp_pcg_2048_converges_and_is_second_order():
+    """The largest plate size of the serving trace, 2048^2: the true residual
+    recomputed by the oracle meets 1e-10 in under a hundred iterations, and
+    the error against the exact solution continues the second-order sequence
+    measured at N = 16, 32, 64 (C h^2 with C from N = 64)."""
+    from oracle import apply as oap
+    n = 2048
+    m, f, g, x = bvp_inputs(n, 2)
+    info = sc.solve_biharmonic(f, g, x, solver="pcg", rtol=RTOL)
+    assert info["status"] == 0 and info["rel_res"] <= RTOL and info["iters"] < 100, info
+    xs = x.cpu().numpy()
+    w = ost.fp_weights(ost.bilaplacian(2, 2), Fraction(1, n + 1), np.float64)
+    b = obvp.rhs_exact_ghost(w, m["g"], m["u_padded"], 2)
+    r = b - oap.apply(w, xs, "zero", 2)
+    absw = {k: abs(v) for k, v in w.items()}
+    slack = 26 * np.finfo(float).eps * np.linalg.norm(oap.apply(absw, np.abs(xs), "zero", 2))
+    assert np.linalg.norm(r) <= RTOL * np.linalg.norm(b) + slack
+    e = np.max(np.abs(xs - m["u_exact"]))
+    e64 = 1.455e-4 * (65.0 / (n + 1)) ** 2  # the N = 64 error scaled by h^2
+    print(f"PCG 2048^2: iters {info['iters']} relres {info['rel_res']:.2e} linf err {e:.3e} (h^2 model {e64:.3e})")
+    assert 0.9 * e64 <= e <= 1.1 * e64
+
+
 def test_bvp_second_order_convergence():
     """Sec. 3.3: second-order convergence of the composed 13-point solve."""
     errs = []
