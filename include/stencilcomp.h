@@ -408,16 +408,22 @@ int sc_selftest_barrier_timeout(void *work_dev, size_t work_bytes, int64_t spin_
  * Resident requests advance together in persistent launches of at most
  * slice_ms milliseconds each (every request on its own group of CTAs);
  * between slices finished requests are retired (their result copied to the
- * caller's host buffer, their memory freed) and newly admitted ones join.  A
- * request's result does not depend on what else is in flight: it is
- * bit-identical to sc_solve_biharmonic / sc_ch_step (batch 1) with the same
- * precision.  The server never allocates device memory: everything lives in
+ * caller's host buffer, their memory freed) and newly admitted ones join.
+ * Plate problems routed to the preconditioned solver (see sc_request.solver)
+ * are admitted from a queue of their own, by the same arena, and solved one at
+ * a time by a second scheduler thread on its own stream.  A request's result
+ * does not depend on what else is in flight: it is bit-identical to
+ * sc_solve_biharmonic (with the same solver and precision) / sc_ch_step
+ * (batch 1).  The server never allocates device memory: everything lives in
  * the arena. */
 typedef struct {
   void *arena_dev;     /* device memory owned by the caller                   */
   size_t arena_bytes;  /* its size: the admission budget                     */
   int32_t max_active;  /* resident requests at most (1..4096)                */
   double slice_ms;     /* length of one persistent launch (> 0)              */
+  int64_t pcg_min_points; /* plate requests with solver -1 go to the
+                          preconditioned solver from this many grid points
+                          on (0: 65536)                                     */
   int32_t fail_slice;  /* failure-detection test hook, normally 0: with k > 0
                           the scheduler treats its k-th time slice as failed
                           (as if the launch had returned an error; nothing is
@@ -437,6 +443,13 @@ typedef enum {
  * n (n^ndim values) and x_host receiving the field at step n + 1. */
 typedef struct {
   int32_t kind;        /* sc_request_kind                                   */
+  int32_t solver;      /* plate problems: SC_SOLVER_PERSISTENT (batched with
+                          the other resident requests), SC_SOLVER_PCG (the
+                          preconditioned solver, one request at a time on a
+                          second scheduler thread, concurrently with the
+                          batched slices), or -1: SC_SOLVER_PCG for grids of at
+                          least sc_server_cfg.pcg_min_points points, else
+                          batched.  Cahn-Hilliard steps are always batched.   */
   int32_t ndim;
   int32_t order;
   int64_t n[3];
@@ -464,7 +477,8 @@ typedef struct {
 
 typedef struct sc_server sc_server;
 
-/* Device bytes a request occupies while resident (fields + Krylov state). */
+/* Device bytes a request occupies while resident (fields + Krylov state),
+ * for the default routing of solver -1 (65536 points). */
 size_t sc_request_bytes(const sc_request *req);
 int sc_server_create(const sc_server_cfg *cfg, sc_server **out);
 /* Stops the scheduler; requests still queued or resident are abandoned. */

@@ -108,15 +108,23 @@ static long long padded_of(const sc_request *r, int R) {
   return n;
 }
 
+// The solver a plate request runs on (the size rule of sc_request.solver).
+constexpr long long PCG_MIN_POINTS = 1LL << 16;
+static int plate_solver(const sc_request *r, long long min_pts) {
+  if (r->solver == SC_SOLVER_PERSISTENT || r->solver == SC_SOLVER_PCG) return r->solver;
+  return npts_of(r) >= min_pts ? SC_SOLVER_PCG : SC_SOLVER_PERSISTENT;
+}
+
 // Plate problem view of a request (device pointers filled in at admission).
-static sc_bvp as_bvp(const sc_request *r, const double *f, const double *g, double *x) {
+static sc_bvp as_bvp(const sc_request *r, const double *f, const double *g, double *x,
+                     long long min_pts = PCG_MIN_POINTS) {
   sc_bvp b;
   std::memset(&b, 0, sizeof(b));
   b.ndim = r->ndim;
   b.order = r->order;
   for (int a = 0; a < 3; ++a) b.n[a] = r->n[a];
   b.prec = r->prec;
-  b.solver = SC_SOLVER_PERSISTENT;
+  b.solver = plate_solver(r, min_pts);
   b.rtol = r->rtol;
   b.maxit = r->maxit;
   b.f_dev = f;
@@ -150,20 +158,23 @@ static sc_ch as_ch(const sc_request *r) {
 }
 
 // The request's spec with device pointers placed at x (f, g for a plate).
-static int request_spec(const sc_request *r, double *f, double *g, double *x, ProbSpec &sp) {
+static int request_spec(const sc_request *r, double *f, double *g, double *x, ProbSpec &sp,
+                        long long min_pts) {
   if (r->kind == SC_REQ_CH) {
     sc_ch c = as_ch(r);
     return ch_single_spec(&c, x, sp);
   }
   if (r->kind != SC_REQ_PLATE) return fail(SC_EINVAL, "unknown request kind %d", r->kind);
-  sc_bvp b = as_bvp(r, f, g, x);
+  if (r->solver != -1 && r->solver != SC_SOLVER_PERSISTENT && r->solver != SC_SOLVER_PCG)
+    return fail(SC_EINVAL, "request solver must be -1, SC_SOLVER_PERSISTENT or SC_SOLVER_PCG");
+  sc_bvp b = as_bvp(r, f, g, x, min_pts);
   return bvp_spec(&b, sp);
 }
 
-static int request_layout(const sc_request *r, ProbSpec &sp, size_t *bytes) {
+static int request_layout(const sc_request *r, ProbSpec &sp, size_t *bytes, long long min_pts) {
   // validation with placeholder pointers (never dereferenced)
   static double dummy;
-  if (int rc = request_spec(r, &dummy, &dummy, &dummy, sp)) return rc;
+  if (int rc = request_spec(r, &dummy, &dummy, &dummy, sp, min_pts)) return rc;
   Carver cv(nullptr, 0);
   if (r->kind == SC_REQ_PLATE) {
     cv.take(npts_of(r) * 8);          // f
@@ -194,6 +205,11 @@ struct sc_server {
   std::condition_variable cv_work, cv_done;
   std::deque<sc::Req *> pending;
   std::vector<sc::Req *> active;
+  std::deque<sc::Req *> pcg_pending;  // plate requests for the preconditioned solver
+  sc::Req *pcg_active = nullptr;
+  long long min_pts = 1LL << 16;
+  cudaStream_t st2 = nullptr;
+  std::thread pcg_worker;
   std::unordered_map<uint64_t, sc::Req *> all;
   uint64_t next_id = 1;
   bool stop = false;
@@ -214,6 +230,82 @@ static void retire(sc_server *S, Req *r, const SolveState &st) {
   r->res.rel_res = st.rel;
   r->res.queue_s = r->t_admit - r->t_submit;
   r->res.latency_s = r->t_done - r->t_submit;
+}
+
+// Copies a request's fields into its arena space and enqueues its
+// right-hand side on `st` (synchronous for the host buffers it reads).
+static int setup_request(sc_server *S, Req *r, cudaStream_t st) {
+  Carver cv(S->arena_base + r->off, r->bytes);
+  const long long n = npts_of(&r->rq);
+  const bool plate = r->rq.kind == SC_REQ_PLATE;
+  if (plate) {
+    const long long np = padded_of(&r->rq, r->sp.R);
+    r->f = static_cast<double *>(cv.take(n * 8));
+    r->g = static_cast<double *>(cv.take(np * 8));
+    cudaMemcpyAsync(r->f, r->rq.f_host, n * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(r->g, r->rq.ghost_host, np * 8, cudaMemcpyHostToDevice, st);
+  }
+  r->x = static_cast<double *>(cv.take(n * 8));
+  if (!plate) cudaMemcpyAsync(r->x, r->rq.u_host, n * 8, cudaMemcpyHostToDevice, st);
+  r->sp.x = r->x;
+  layout(r->sp, cv, r->P, r->aux);
+  int rc = upload_prob(r->sp, r->P, r->aux, st);
+  if (!rc && plate) {
+    sc_bvp b = as_bvp(&r->rq, r->f, r->g, r->x, S->min_pts);
+    rc = setup_bvp(&b, r->sp, r->P, r->aux, st);
+  } else if (!rc) {
+    sc_ch c = as_ch(&r->rq);
+    rc = setup_ch(&c, r->sp, r->P, r->aux, st);
+  }
+  r->t_admit = now_s();
+  return rc;
+}
+
+// Second scheduler: plate requests for the preconditioned solver, one at a
+// time in arrival order (skipping those that do not fit yet), on st2.
+static void pcg_loop(sc_server *S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    Req *r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || !S->pcg_pending.empty(); });
+      if (S->stop) return;
+      for (auto it = S->pcg_pending.begin(); it != S->pcg_pending.end(); ++it) {
+        size_t off;
+        if (S->arena.alloc((*it)->bytes, &off)) {
+          r = *it;
+          r->off = off;
+          S->pcg_pending.erase(it);
+          S->pcg_active = r;
+          break;
+        }
+      }
+    }
+    if (!r) continue;
+    int rc = setup_request(S, r, S->st2);
+    double res[3] = {0.0, 0.0, double(SC_OK)};
+    if (!rc) rc = run_pcg(r->sp, r->P, r->aux, S->st2, res);
+    if (!rc) {
+      cudaError_t e = cudaMemcpyAsync(r->rq.x_host, r->x, npts_of(&r->rq) * 8, cudaMemcpyDeviceToHost, S->st2);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(S->st2);
+      if (e != cudaSuccess) rc = fail(SC_ECUDA, "result copy: %s", cudaGetErrorString(e));
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(&r->res, 0, sizeof(r->res));
+    r->t_done = now_s();
+    r->res.status = rc ? rc : int(res[2]);
+    r->res.prec = SC_PREC_F64;
+    r->res.iters = (long long)res[0];
+    r->res.rel_res = res[1];
+    r->res.queue_s = r->t_admit - r->t_submit;
+    r->res.latency_s = r->t_done - r->t_submit;
+    r->done = true;
+    if (rc == SC_ECUDA && !S->worker_error) S->worker_error = rc;
+    S->arena.release(r->off, r->bytes);
+    S->pcg_active = nullptr;
+    S->cv_done.notify_all();
+  }
 }
 
 static void worker_loop(sc_server *S) {
@@ -243,29 +335,7 @@ static void worker_loop(sc_server *S) {
     }
     // set up admitted requests (outside the lock)
     for (Req *r : admit) {
-      Carver cv(S->arena_base + r->off, r->bytes);
-      const long long n = npts_of(&r->rq);
-      const bool plate = r->rq.kind == SC_REQ_PLATE;
-      if (plate) {
-        const long long np = padded_of(&r->rq, r->sp.R);
-        r->f = static_cast<double *>(cv.take(n * 8));
-        r->g = static_cast<double *>(cv.take(np * 8));
-        cudaMemcpyAsync(r->f, r->rq.f_host, n * 8, cudaMemcpyHostToDevice, S->st);
-        cudaMemcpyAsync(r->g, r->rq.ghost_host, np * 8, cudaMemcpyHostToDevice, S->st);
-      }
-      r->x = static_cast<double *>(cv.take(n * 8));
-      if (!plate) cudaMemcpyAsync(r->x, r->rq.u_host, n * 8, cudaMemcpyHostToDevice, S->st);
-      r->sp.x = r->x;
-      layout(r->sp, cv, r->P, r->aux);
-      int rc = upload_prob(r->sp, r->P, r->aux, S->st);
-      if (!rc && plate) {
-        sc_bvp b = as_bvp(&r->rq, r->f, r->g, r->x);
-        rc = setup_bvp(&b, r->sp, r->P, r->aux, S->st);
-      } else if (!rc) {
-        sc_ch c = as_ch(&r->rq);
-        rc = setup_ch(&c, r->sp, r->P, r->aux, S->st);
-      }
-      r->t_admit = now_s();
+      const int rc = setup_request(S, r, S->st);
       std::lock_guard<std::mutex> lk(S->mu);
       if (rc) {
         std::memset(&r->res, 0, sizeof(r->res));
@@ -342,7 +412,7 @@ size_t sc_request_bytes(const sc_request *req) {
   if (!req) return 0;
   ProbSpec sp;
   size_t b = 0;
-  if (request_layout(req, sp, &b)) return 0;
+  if (request_layout(req, sp, &b, PCG_MIN_POINTS)) return 0;
   return b;
 }
 
@@ -351,6 +421,7 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
   if (cfg->max_active < 1 || cfg->max_active > 4096) return fail(SC_EINVAL, "max_active must be 1..4096");
   if (!(cfg->slice_ms > 0.0)) return fail(SC_EINVAL, "slice_ms must be positive");
   if (cfg->fail_slice < 0) return fail(SC_EINVAL, "fail_slice must be >= 0");
+  if (cfg->pcg_min_points < 0) return fail(SC_EINVAL, "pcg_min_points must be >= 0");
   // the CTA -> problem map must hold the largest grid any persistent-kernel
   // variant can launch: bound it by the hardware limit of resident CTAs
   const int G = 32 * num_sms();
@@ -363,8 +434,14 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
   if (cfg->arena_bytes <= hbytes + 4096) return fail(SC_ENOMEM, "arena smaller than the server's descriptors");
   sc_server *S = new sc_server();
   S->cfg = *cfg;
+  if (cfg->pcg_min_points > 0) S->min_pts = cfg->pcg_min_points;
   cudaGetDevice(&S->device);
   if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete S;
+    return fail(SC_ECUDA, "stream creation failed");
+  }
+  if (cudaStreamCreateWithFlags(&S->st2, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStreamDestroy(S->st);
     delete S;
     return fail(SC_ECUDA, "stream creation failed");
   }
@@ -377,6 +454,7 @@ int sc_server_create(const sc_server_cfg *cfg, sc_server **out) {
   S->arena_size = cfg->arena_bytes - hbytes;
   S->arena.reset(S->arena_size);
   S->worker = std::thread(worker_loop, S);
+  S->pcg_worker = std::thread(pcg_loop, S);
   *out = S;
   clear_error();
   return SC_OK;
@@ -390,8 +468,11 @@ int sc_server_destroy(sc_server *S) {
   }
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  if (S->pcg_worker.joinable()) S->pcg_worker.join();
   cudaStreamSynchronize(S->st);
+  cudaStreamSynchronize(S->st2);
   cudaStreamDestroy(S->st);
+  cudaStreamDestroy(S->st2);
   for (auto &kv : S->all) delete kv.second;
   delete S;
   clear_error();
@@ -409,7 +490,7 @@ int sc_submit(sc_server *S, const sc_request *req, uint64_t *ticket) {
   if (req->kind == SC_REQ_CH && !req->u_host) return fail(SC_EINVAL, "null host buffer");
   Req *r = new Req();
   r->rq = *req;
-  if (int rc = request_layout(req, r->sp, &r->bytes)) {
+  if (int rc = request_layout(req, r->sp, &r->bytes, S->min_pts)) {
     delete r;
     return rc;
   }
@@ -422,7 +503,10 @@ int sc_submit(sc_server *S, const sc_request *req, uint64_t *ticket) {
     std::lock_guard<std::mutex> lk(S->mu);
     r->id = S->next_id++;
     S->all[r->id] = r;
-    S->pending.push_back(r);
+    if (r->sp.solver == SC_SOLVER_PCG)
+      S->pcg_pending.push_back(r);
+    else
+      S->pending.push_back(r);
     *ticket = r->id;
   }
   S->cv_work.notify_all();
@@ -451,8 +535,8 @@ int sc_server_status(sc_server *S, int32_t *worker_error, size_t *free_bytes, si
   if (worker_error) *worker_error = S->worker_error;
   if (free_bytes) *free_bytes = S->arena.free_total();
   if (arena_bytes) *arena_bytes = S->arena_size;
-  if (active) *active = int32_t(S->active.size());
-  if (pending) *pending = int32_t(S->pending.size());
+  if (active) *active = int32_t(S->active.size() + (S->pcg_active ? 1 : 0));
+  if (pending) *pending = int32_t(S->pending.size() + S->pcg_pending.size());
   clear_error();
   return SC_OK;
 }
@@ -461,7 +545,10 @@ int sc_server_drain(sc_server *S, double timeout_s) {
   if (!S) return fail(SC_EINVAL, "null server");
   std::unique_lock<std::mutex> lk(S->mu);
   const bool ok = S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
-                                      [&] { return S->pending.empty() && S->active.empty(); });
+                                      [&] {
+                                        return S->pending.empty() && S->active.empty() && S->pcg_pending.empty() &&
+                                               !S->pcg_active;
+                                      });
   if (!ok) return fail(SC_ETIMEOUT, "requests still in flight after %.3f s", timeout_s);
   clear_error();
   return SC_OK;

@@ -18,11 +18,13 @@ REQ_PLATE, REQ_CH = 0, 1
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("arena_dev", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
-                ("max_active", ctypes.c_int32), ("slice_ms", ctypes.c_double), ("fail_slice", ctypes.c_int32)]
+                ("max_active", ctypes.c_int32), ("slice_ms", ctypes.c_double), ("pcg_min_points", ctypes.c_int64),
+                ("fail_slice", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("ndim", ctypes.c_int32), ("order", ctypes.c_int32),
+    _fields_ = [("kind", ctypes.c_int32), ("solver", ctypes.c_int32), ("ndim", ctypes.c_int32),
+                ("order", ctypes.c_int32),
                 ("n", ctypes.c_int64 * 3), ("prec", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int64), ("f_host", ctypes.c_void_p), ("ghost_host", ctypes.c_void_p),
                 ("u_host", ctypes.c_void_p), ("h_num", ctypes.c_int64), ("h_den", ctypes.c_int64),
@@ -65,12 +67,17 @@ def _host_f64(*arrays):
             raise ValueError("host buffers must be C-contiguous float64 arrays")
 
 
+_RSOLVER = {"auto": -1, "persistent": 0, "pcg": 2}
+
+
 def make_request(f: np.ndarray, ghost: np.ndarray, x: np.ndarray, order=2, prec="auto", rtol=1e-10,
-                 maxit=10_000_000) -> Request:
-    """A plate problem (Sec. 3.3): f and the ghosted exact field in, x out."""
+                 maxit=10_000_000, solver="auto") -> Request:
+    """A plate problem (Sec. 3.3): f and the ghosted exact field in, x out.
+    solver: "persistent" (batched), "pcg" (preconditioned) or "auto" (by size)."""
     _host_f64(f, ghost, x)
     r = Request()
     r.kind = REQ_PLATE
+    r.solver = _RSOLVER[solver] if isinstance(solver, str) else int(solver)
     r.ndim, r.order = x.ndim, order
     for a, s in enumerate(reversed(x.shape)):
         r.n[a] = s
@@ -88,6 +95,7 @@ def make_ch_request(u: np.ndarray, x: np.ndarray, h, dt, M=1.0, kappa=1e-4, chem
         raise ValueError("u and x must have the same shape")
     r = Request()
     r.kind = REQ_CH
+    r.solver = 0
     r.ndim, r.order = x.ndim, order
     for a, s in enumerate(reversed(x.shape)):
         r.n[a] = s
@@ -109,11 +117,13 @@ class Server:
     """Continuous-batching server of plate problems and Cahn-Hilliard steps on
     the current device."""
 
-    def __init__(self, arena: torch.Tensor, max_active: int = 256, slice_ms: float = 2.0, fail_slice: int = 0):
+    def __init__(self, arena: torch.Tensor, max_active: int = 256, slice_ms: float = 2.0, fail_slice: int = 0,
+                 pcg_min_points: int = 0):
         if not arena.is_cuda:
             raise ValueError("arena must be a CUDA tensor")
         self._arena = arena
-        cfg = ServerCfg(arena.data_ptr(), arena.numel() * arena.element_size(), max_active, slice_ms, fail_slice)
+        cfg = ServerCfg(arena.data_ptr(), arena.numel() * arena.element_size(), max_active, slice_ms,
+                        pcg_min_points, fail_slice)
         h = ctypes.c_void_p()
         check(lib.sc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

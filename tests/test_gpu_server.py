@@ -26,10 +26,10 @@ def _case(n, ndim, ks):
     return np.ascontiguousarray(m["g"]), np.ascontiguousarray(m["u_padded"])
 
 
-def _solo(f, g, prec):
+def _solo(f, g, prec, solver="persistent"):
     ft, gt = torch.from_numpy(f).to(DEV), torch.from_numpy(g).to(DEV)
     x = torch.empty(f.shape, dtype=torch.float64, device=DEV)
-    info = sc.solve_biharmonic(ft, gt, x, prec=prec, rtol=1e-10)
+    info = sc.solve_biharmonic(ft, gt, x, prec=prec, solver=solver, rtol=1e-10)
     return x.cpu().numpy(), info
 
 
@@ -206,3 +206,34 @@ def test_failed_time_slice_frees_the_arena_and_refuses_new_work():
     f, g = _case(16, 2, (1, 1))
     solo, info = _solo(f, g, "f64")
     assert info["status"] == 0 and info["rel_res"] <= 1e-10
+
+
+def test_large_plates_go_to_the_preconditioned_solver_alongside_batched_ones():
+    """Plate problems of at least 2^16 points are routed (by the automatic
+    rule) to the preconditioned solver on the server's second scheduler
+    thread while small ones are batched: every result equals its solo solve
+    with the same solver, bit for bit, and the large ones take tens of
+    iterations."""
+    arena = torch.empty(2 << 30, dtype=torch.uint8, device=DEV)
+    srv = sc.Server(arena, max_active=64, slice_ms=1.0)
+    try:
+        jobs = []
+        for n, nd, ks in [(300, 2, (1, 2)), (40, 2, (1, 1)), (41, 3, (1, 1, 2)), (24, 2, (3, 2)), (512, 2, (2, 1)),
+                          (12, 3, (1, 2, 1))]:
+            f, g = _case(n, nd, ks)
+            x = np.full(f.shape, np.nan)
+            big = f.size >= (1 << 16)
+            jobs.append((big, srv.submit(f, g, x, prec="f64"), f, g, x))
+        srv.drain(300.0)
+        for big, t, f, g, x in jobs:
+            r = srv.poll(t)
+            assert r is not None and r["status"] == 0 and r["rel_res"] <= 1e-10, r
+            solo, info = _solo(f, g, "f64", "pcg" if big else "persistent")
+            assert info["iters"] == r["iters"]
+            if big:
+                assert r["iters"] <= 80
+            assert np.array_equal(solo, x)
+        st = srv.status()
+        assert st["free_bytes"] == st["arena_bytes"] and st["active"] == 0 and st["pending"] == 0
+    finally:
+        srv.close()
