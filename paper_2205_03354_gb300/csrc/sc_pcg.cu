@@ -48,29 +48,40 @@ struct GemmArgs {
   int M, N, K;
   long long lda, ldb, ldc;
   long long sa, sb, sc;  // batch strides (0: shared operand)
+  int ksplit = 1;        // > 1: K in ksplit slices, slice s of batch b written
+  T *part = nullptr;     // densely to part[(s * batch + b) * M * N], then summed
+  int batch = 1;
 };
 
 template <typename T>
 __global__ void __launch_bounds__(GM_NTHR) k_gemm(GemmArgs<T> g) {
   __shared__ T As[GM_BK][GM_BM + 4];  // transposed: As[k][m]
   __shared__ T Bs[GM_BK][GM_BN + 4];
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / g.ksplit, ks = blockIdx.z % g.ksplit;
   const T *A = g.A + b * g.sa, *B = g.B + b * g.sb;
   T *C = g.C + b * g.sc;
+  long long ldc = g.ldc;
+  if (g.ksplit > 1) {
+    C = g.part + ((long long)ks * g.batch + b) * g.M * g.N;
+    ldc = g.N;
+  }
+  // this slice's K range, in whole tiles
+  const int kt = (g.K + GM_BK - 1) / GM_BK, kper = (kt + g.ksplit - 1) / g.ksplit;
+  const int kbeg = ks * kper * GM_BK, kend = min(g.K, (ks + 1) * kper * GM_BK);
   const int m0 = blockIdx.y * GM_BM, n0 = blockIdx.x * GM_BN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 outputs each
   T acc[4][4] = {};
-  for (int k0 = 0; k0 < g.K; k0 += GM_BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += GM_BK) {
     // A tile: 64 x 16 (4 per thread); B tile: 16 x 64 (4 per thread)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int e = threadIdx.x + i * GM_NTHR;
       const int am = e / GM_BK, ak = e % GM_BK;
       const int gm = m0 + am, gk = k0 + ak;
-      As[ak][am] = (gm < g.M && gk < g.K) ? A[(long long)gm * g.lda + gk] : T(0);
+      As[ak][am] = (gm < g.M && gk < kend) ? A[(long long)gm * g.lda + gk] : T(0);
       const int bk = e / GM_BN, bn = e % GM_BN;
       const int hk = k0 + bk, hn = n0 + bn;
-      Bs[bk][bn] = (hk < g.K && hn < g.N) ? B[(long long)hk * g.ldb + hn] : T(0);
+      Bs[bk][bn] = (hk < kend && hn < g.N) ? B[(long long)hk * g.ldb + hn] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -94,15 +105,123 @@ __global__ void __launch_bounds__(GM_NTHR) k_gemm(GemmArgs<T> g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx * 4 + j;
+      if (gn < g.N) C[(long long)gm * ldc + gn] = acc[i][j];
+    }
+  }
+}
+
+// FP32 GEMM for the large transforms: 128 x 128 output tiles, K in steps of
+// 8, 256 threads with 8 x 8 outputs each (two 4 x 4 quadrants, so that the
+// shared-memory reads are broadcasts / consecutive 16-byte words); the next
+// K step is loaded into registers while the current one is multiplied (two
+// shared buffers, one barrier per step).  Edges are predicated.
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8, SG_PAD = 4;
+
+__global__ void __launch_bounds__(256) k_sgemm128(GemmArgs<float> g) {
+  __shared__ __align__(16) float As[2][SG_BK][SG_BM + SG_PAD];
+  __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
+  const int b = blockIdx.z;
+  const float *A = g.A + b * g.sa, *B = g.B + b * g.sb;
+  float *C = g.C + b * g.sc;
+  const int m0 = blockIdx.y * SG_BM, n0 = blockIdx.x * SG_BN;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      const int am = e / SG_BK, ak = e % SG_BK, gm = m0 + am, gk = k0 + ak;
+      ra[i] = (gm < g.M && gk < g.K) ? __ldg(A + (long long)gm * g.lda + gk) : 0.0f;
+      const int bk = e / SG_BN, bn = e % SG_BN, hk = k0 + bk, hn = n0 + bn;
+      rb[i] = (hk < g.K && hn < g.N) ? __ldg(B + (long long)hk * g.ldb + hn) : 0.0f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      As[buf][e % SG_BK][e / SG_BK] = ra[i];
+      Bs[buf][e / SG_BN][e % SG_BN] = rb[i];
+    }
+  };
+  float acc[8][8] = {};
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < g.K; k0 += SG_BK) {
+    const bool more = k0 + SG_BK < g.K;
+    if (more) fetch(k0 + SG_BK);
+#pragma unroll
+    for (int k = 0; k < SG_BK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      stash(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
       if (gn < g.N) C[(long long)gm * g.ldc + gn] = acc[i][j];
     }
   }
 }
 
+// C[b] = sum over slices s of part[s][b] (fixed order: deterministic).
 template <typename T>
-static void gemm(const GemmArgs<T> &g, int batch, cudaStream_t st) {
-  dim3 grid((g.N + GM_BN - 1) / GM_BN, (g.M + GM_BM - 1) / GM_BM, batch);
+__global__ void k_gemm_reduce(GemmArgs<T> g) {
+  const long long mn = (long long)g.M * g.N, n = mn * g.batch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / mn, e = i % mn, m = e / g.N, c = e % g.N;
+    T s = T(0);
+    for (int k = 0; k < g.ksplit; ++k) s += g.part[(long long)k * n + i];
+    g.C[b * g.sc + m * g.ldc + c] = s;
+  }
+}
+
+template <typename T>
+static void gemm(GemmArgs<T> g, int batch, cudaStream_t st, T *part = nullptr, long long part_cap = 0) {
+  const long long ctas = (long long)((g.N + GM_BN - 1) / GM_BN) * ((g.M + GM_BM - 1) / GM_BM) * batch;
+  // FP64 tiles are slow per SM: split K until about two CTAs per SM
+  int ks = 1;
+  if (part && sizeof(T) == 8) {
+    const long long want = (2LL * num_sms() + ctas - 1) / ctas;
+    ks = int(std::max<long long>(1, std::min<long long>(want, g.K / (4 * GM_BK))));
+    while (ks > 1 && (long long)ks * g.M * g.N * batch > part_cap) --ks;
+  }
+  g.ksplit = ks;
+  g.part = part;
+  g.batch = batch;
+  if constexpr (sizeof(T) == 4) {
+    if (g.M >= SG_BM && g.N >= SG_BN) {
+      dim3 grid128((g.N + SG_BN - 1) / SG_BN, (g.M + SG_BM - 1) / SG_BM, batch);
+      k_sgemm128<<<grid128, 256, 0, st>>>(g);
+      return;
+    }
+  }
+  dim3 grid((g.N + GM_BN - 1) / GM_BN, (g.M + GM_BM - 1) / GM_BM, batch * ks);
   k_gemm<T><<<grid, GM_NTHR, 0, st>>>(g);
+  if (ks > 1) {
+    const long long n = (long long)g.M * g.N * batch;
+    k_gemm_reduce<T><<<int(std::min<long long>((n + 255) / 256, 8LL * num_sms())), 256, 0, st>>>(g);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -295,26 +414,31 @@ static void dst_all(float *u, float *w, const float *S, int N, int ndim, cudaStr
 
 int pcg_low_modes(int ndim, long long N) { return int(std::min<long long>(N, ndim == 3 ? 16 : 64)); }
 
+// FP64 GEMM with split-K partials in the preconditioner's work space.
+static void gemmd(const ProbAux &aux, const GemmArgs<double> &g, int batch, cudaStream_t st) {
+  gemm<double>(g, batch, st, aux.gp, aux.gp_cap);
+}
+
 // zl = S_low^T Lambda^-2 S_low r over the K0^ndim lowest modes, in FP64.
 static void precond_low(const double *r, const ProbAux &aux, int N, int K0, int ndim, cudaStream_t st) {
   const long long N2 = (long long)N * N, K2 = (long long)K0 * K0;
   if (ndim == 2) {
-    gemm(GemmArgs<double>{r, aux.SlT, aux.wa, N, K0, N, N, K0, K0, 0, 0, 0}, 1, st);        // (y, kx)
-    gemm(GemmArgs<double>{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, 0, 0}, 1, st);   // (ky, kx)
+    gemmd(aux, GemmArgs<double>{r, aux.SlT, aux.wa, N, K0, N, N, K0, K0, 0, 0, 0}, 1, st);        // (y, kx)
+    gemmd(aux, GemmArgs<double>{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, 0, 0}, 1, st);   // (ky, kx)
     k_low_scale<<<grid_for(K2), 256, 0, st>>>(aux.wb, aux.lam1, K0, 2);
-    gemm(GemmArgs<double>{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, 0, 0}, 1, st);  // (y, kx)
-    gemm(GemmArgs<double>{aux.wa, aux.Sl, aux.zl, N, N, K0, K0, N, N, 0, 0, 0}, 1, st);      // (y, x)
+    gemmd(aux, GemmArgs<double>{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, 0, 0}, 1, st);  // (y, kx)
+    gemmd(aux, GemmArgs<double>{aux.wa, aux.Sl, aux.zl, N, N, K0, K0, N, N, 0, 0, 0}, 1, st);      // (y, x)
     return;
   }
-  gemm(GemmArgs<double>{r, aux.SlT, aux.wa, int(N2), K0, N, N, K0, K0, 0, 0, 0}, 1, st);     // (z, y, kx)
-  gemm(GemmArgs<double>{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, (long long)N * K0, K2}, N,
+  gemmd(aux, GemmArgs<double>{r, aux.SlT, aux.wa, int(N2), K0, N, N, K0, K0, 0, 0, 0}, 1, st);     // (z, y, kx)
+  gemmd(aux, GemmArgs<double>{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, (long long)N * K0, K2}, N,
        st);                                                                                  // (z, ky, kx)
-  gemm(GemmArgs<double>{aux.Sl, aux.wb, aux.wc, K0, int(K2), N, N, K2, K2, 0, 0, 0}, 1, st);  // (kz, ky, kx)
+  gemmd(aux, GemmArgs<double>{aux.Sl, aux.wb, aux.wc, K0, int(K2), N, N, K2, K2, 0, 0, 0}, 1, st);  // (kz, ky, kx)
   k_low_scale<<<grid_for(K2 * K0), 256, 0, st>>>(aux.wc, aux.lam1, K0, 3);
-  gemm(GemmArgs<double>{aux.SlT, aux.wc, aux.wb, N, int(K2), K0, K0, K2, K2, 0, 0, 0}, 1, st);  // (z, ky, kx)
-  gemm(GemmArgs<double>{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, K2, (long long)N * K0}, N,
+  gemmd(aux, GemmArgs<double>{aux.SlT, aux.wc, aux.wb, N, int(K2), K0, K0, K2, K2, 0, 0, 0}, 1, st);  // (z, ky, kx)
+  gemmd(aux, GemmArgs<double>{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, K2, (long long)N * K0}, N,
        st);                                                                                  // (z, y, kx)
-  gemm(GemmArgs<double>{aux.wa, aux.Sl, aux.zl, int(N2), N, K0, K0, N, N, 0, 0, 0}, 1, st);    // (z, y, x)
+  gemmd(aux, GemmArgs<double>{aux.wa, aux.Sl, aux.zl, int(N2), N, K0, K0, N, N, 0, 0, 0}, 1, st);    // (z, y, x)
 }
 
 // z = M^-1 r = S Lambda^-2 S r: the lowest modes in FP64, the rest in FP32.
