@@ -27,6 +27,8 @@ from .cg import cg
 def fprime(c: np.ndarray, chem: tuple) -> np.ndarray:
     if chem[0] == "cubic":
         return c ** 3 - c
+    if chem[0] == "linear":  # f(c) = a c^2 / 2: a linear model used to pin the time steppers
+        return chem[1] * c
     if chem[0] == "double_well":
         _, rho, ca, cb = chem
         return 2.0 * rho * (c - ca) * (c - cb) * (2.0 * c - ca - cb)
@@ -108,3 +110,39 @@ def free_energy(c: np.ndarray, h: float, kappa: float, chem: tuple) -> float:
         d = (np.roll(c, -1, axis=ax) - c) / h
         grad2 += d * d
     return float(h ** c.ndim * np.sum(fchem(c, chem) + 0.5 * kappa * grad2))
+
+
+# Semi-implicit backward differentiation (SBDF) schemes of orders 1-3 for the
+# same splitting (the paper uses IMEX schemes of orders one to three in Sec.
+# 4.3 without naming them; these are the standard SBDF family).  With
+# history u^n, u^(n-1), ... and N(u) = M Lap f'(u):
+#   sum_j a_j u^(n+1-j) / dt = -M kappa Lap Lap u^(n+1) + sum_j b_j N(u^(n-j)),
+# the BDF coefficients a for the implicit part and the extrapolation b for
+# the explicit part.  Divided by a_0:
+#   (I + g dt M kappa Lap Lap) u^(n+1) = sum_j al_j u^(n-j) + g dt M Lap sum_j b_j f'(u^(n-j))
+# with g = 1 / a_0 and al_j = -a_(j+1) / a_0.
+SBDF = {
+    1: {"a": (1.0, -1.0), "b": (1.0,)},
+    2: {"a": (1.5, -2.0, 0.5), "b": (2.0, -1.0)},
+    3: {"a": (11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0), "b": (3.0, -3.0, 1.0)},
+}
+
+
+def sbdf_coefficients(order: int):
+    """(al, b, g) of the divided form above."""
+    a, b = SBDF[order]["a"], SBDF[order]["b"]
+    g = 1.0 / a[0]
+    al = tuple(-a[j + 1] / a[0] for j in range(order))
+    return al, b, g
+
+
+def step_sbdf_fft(hist: list, h: float, dt: float, M: float, kappa: float, chem: tuple, order: int,
+                  lap_order: int = 2) -> np.ndarray:
+    """One SBDF step from hist = [u^n, u^(n-1), ...] (order fields), solved
+    exactly in the DFT basis where the periodic operators are diagonal."""
+    al, b, g = sbdf_coefficients(order)
+    lam = lap_symbol(hist[0].shape, h, lap_order)
+    rhs = sum(al[j] * np.fft.fftn(hist[j]) for j in range(order))
+    nl = sum(b[j] * np.fft.fftn(fprime(hist[j], chem)) for j in range(order))
+    new = (rhs + g * dt * M * lam * nl) / (1.0 + g * dt * M * kappa * lam * lam)
+    return np.real(np.fft.ifftn(new))

@@ -104,3 +104,47 @@ def test_free_energy_of_a_fourier_mode(chem, ndim, n, k, h, kappa, A):
         u = np.broadcast_to((A * np.cos(2 * np.pi * k * i / n)).reshape(shape), (n,) * ndim).copy()
         F = ch.free_energy(u, h, kappa, chem)
         assert abs(F - expect) <= 1e-12 * abs(expect), (ax, F, expect)
+
+
+
+def test_sbdf1_is_the_first_order_step():
+    """SBDF of order one is the first-order IMEX step of Sec. 4.1."""
+    u = manufactured.ch_uniform(24, 2, seed=4, amp=0.4)
+    a = ch.step_sbdf_fft([u], 1.0 / 24, 2e-5, 1.0, 0.05 ** 2, ("cubic",), 1)
+    b = ch.step_fft(u, 1.0 / 24, 2e-5, 1.0, 0.05 ** 2, ("cubic",))
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_sbdf_temporal_order_on_a_linear_model(order):
+    """With f'(u) = c u every Fourier mode obeys du/dt = M (c lam - kappa lam^2) u
+    exactly (lam the discrete Laplacian's symbol); started from exact history,
+    the SBDF error at a fixed time falls by 2^order when dt halves."""
+    n, h, M, kappa, cc, T = 16, 1.0, 1.0, 0.5, -0.3, 1.0
+    rng = np.random.default_rng(0)
+    u0 = rng.normal(size=(n, n)) * 0.1
+    lam = ch.lap_symbol((n, n), h)
+    rate = M * (cc * lam - kappa * lam * lam)
+    # keep only the modes whose exact evolution is resolved by the time steps
+    keep = np.abs(rate) <= 1.0
+    u0 = np.real(np.fft.ifftn(np.fft.fftn(u0) * keep))
+    exact = lambda t: np.real(np.fft.ifftn(np.fft.fftn(u0) * np.exp(rate * t)))
+    errs = []
+    for dt in (0.1, 0.05, 0.025):
+        hist = [exact(-j * dt) for j in range(order)]
+        for _ in range(int(round(T / dt))):
+            new = ch.step_sbdf_fft(hist, h, dt, M, kappa, ("linear", cc), order)
+            hist = [new] + hist[:-1]
+        errs.append(np.max(np.abs(hist[0] - exact(T))))
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - order) <= 0.2 for r in rates), (errs, rates)
+
+
+def test_sbdf_conserves_mass():
+    """Sum al_j = 1 and the periodic operators annihilate constants: a step
+    keeps the (common) mass of its history."""
+    u = manufactured.ch_uniform(20, 2, seed=8, amp=0.3)
+    hist = [u, np.roll(u, 1, axis=0), np.roll(u, 3, axis=1)]
+    for order in (2, 3):
+        new = ch.step_sbdf_fft(hist[:order], 1.0 / 20, 1e-5, 1.0, 0.03 ** 2, ("cubic",), order)
+        assert abs(new.sum() - u.sum()) <= 1e-12 * np.abs(u).sum()
