@@ -119,3 +119,12 @@ def apply_at(weights: dict, x: np.ndarray, bc: str, points: np.ndarray, radius: 
                 acc += float(weights[k]) * float(x[tuple(idx)])
         out[n] = acc
     return out
+
+
+def apply_varcoef(outer: dict, inner: dict, m: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = outer(m * inner(x)) on a periodic grid: the composition of Sec.
+    2.2.4 with a pointwise coefficient between the factors (the variable
+    mobility of d/dx(M d/dx(d2/dx2 f)): compose d/dx with d2/dx2, scale by M
+    at each grid point, compose the result with d/dx)."""
+    t = apply(inner, x, "periodic")
+    return apply(outer, np.asarray(m, dtype=np.float64) * t, "periodic")

@@ -157,3 +157,47 @@ def test_apply_at_hand_computed_values():
     assert ap.apply_at(w, x, "zero", pt)[0] == -x[1, 3]
     xg = np.arange(30.0).reshape(5, 6)  # 3 x 4 interior with a ring of width 1
     assert ap.apply_at(w, xg, "ghosted", pt, 1)[0] == xg[2, 5] - xg[2, 4]
+
+
+def test_varcoef_with_constant_coefficient_is_the_composed_stencil():
+    """A constant coefficient m0 between the factors gives m0 times the
+    composed stencil (Eq. C=B(A))."""
+    rng = np.random.default_rng(12)
+    outer = st.embed(st.d1_central2(), 2, 0)
+    inner = st.compose(st.embed(st.d1_central2(), 2, 0), st.embed(st.d2_central2(), 2, 0))
+    wo = {k: float(v) for k, v in outer.coeffs}
+    wi = {k: float(v) for k, v in inner.coeffs}
+    wc = {k: float(v) for k, v in st.compose(outer, inner).coeffs}
+    x = rng.uniform(-1, 1, (12, 17))
+    y = ap.apply_varcoef(wo, wi, np.full(x.shape, 2.5), x)
+    assert np.allclose(y, 2.5 * ap.apply(wc, x, "periodic"), rtol=0, atol=1e-12)
+
+
+def test_varcoef_is_exact_for_quartic_data_and_linear_mobility():
+    """d/dx(M d/dx(d2/dx2 x^4)) with M = a + b x is 24 a + 48 b x, and the
+    central stencils reproduce it exactly (d2c2 x^4 = 12 x^2 + 2 h^2, whose
+    central derivative is 24 x; M times that is quadratic, whose central
+    derivative is exact).  Checked in exact rationals on points away from the
+    periodic seam."""
+    h = Fraction(1, 4)
+    n = 40
+    xs = [h * i for i in range(n)]
+    a, b = Fraction(3, 2), Fraction(-2, 5)
+    d1 = {k[0]: v / h for k, v in st.d1_central2().coeffs}
+    d2 = {k[0]: v / (h * h) for k, v in st.d2_central2().coeffs}
+    f = [xv ** 4 for xv in xs]
+    t1 = {i: sum(w * f[i + o] for o, w in d2.items()) for i in range(2, n - 2)}
+    t2 = {i: sum(w * t1[i + o] for o, w in d1.items()) for i in range(3, n - 3)}
+    mt = {i: (a + b * xs[i]) * t2[i] for i in t2}
+    y = {i: sum(w * mt[i + o] for o, w in d1.items()) for i in range(4, n - 4)}
+    assert all(y[i] == 24 * a + 48 * b * xs[i] for i in y)
+    # the oracle's floating-point evaluation agrees on the same interior points
+    wo = {(k,): float(v) for k, v in d1.items()}
+    wi = {(k,): float(v) for k, v in d2.items()}
+    wi3 = {}
+    for (k1,), v1 in wo.items():
+        for (k2,), v2 in wi.items():
+            wi3[(k1 + k2,)] = wi3.get((k1 + k2,), 0.0) + v1 * v2
+    yo = ap.apply_varcoef(wo, wi3, np.array([float(a + b * xv) for xv in xs]), np.array([float(v) for v in f]))
+    for i in range(6, n - 6):
+        assert abs(yo[i] - float(y[i])) <= 1e-9 * max(1.0, abs(float(y[i])))
