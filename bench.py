@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "f64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-solvers", action="store_true",
+                    help="default workload: skip the solver-configuration records")
     ap.add_argument("--no-serving", action="store_true",
                     help="default workload: skip the short served-vs-plain solve comparison")
     ap.add_argument("--tuning", default="",
@@ -612,6 +614,120 @@ def run_serving(args, local):
             "server_end_state": st, "sizes": {"2d": [lo2, hi2], "3d": [lo3, hi3]}}
 
 
+def run_solver_configs(local):
+    """Bounded records of the solver configurations, each timed with CUDA
+    events on the launching stream and run under one clock sampler:
+      plate 64^2 (13-point Lap o Lap, CG to 1e-10): persistent FP64 and the
+        preconditioned solver, time per solve, iterations, l-inf error;
+      Cahn-Hilliard 1024^2 (eps 0.01, dt 1e-6, u0 uniform +-0.05): 20 steps,
+        per-step iterations and time, mass drift;
+      Cahn-Hilliard 8 x 256^3 (25-point operator, eps 0.02, dt 1e-6): 5 steps
+        in one persistent launch each, per-step free energy of every field,
+        asserted non-increasing, mass drift;
+      the paper's spinodal benchmark (Sec. 4.1-4.2: kappa 2, M 5, rho 5,
+        c_a 0.3, c_b 0.7, cosine initial data, h = 1): 2D 200^2 with dt 0.05 to
+        t = 100 and 3D 64^3 with dt 0.25 to t = 100, graph-replayed in chunks
+        with the free energy after each chunk, asserted non-increasing."""
+    import numpy as np
+    import torch
+    import paper_2205_03354_gb300 as sc
+    from synth_inputs import manufactured
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream()
+    out = {}
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        r = fn()
+        b.record(st)
+        b.synchronize()
+        return r, a.elapsed_time(b)
+
+    with ClockSampler(local) as clk:
+        # plate 64^2
+        m = manufactured.bvp_case(64, 2, 2)
+        f = torch.from_numpy(m["g"]).to(dev)
+        g = torch.from_numpy(m["u_padded"]).to(dev)
+        x = torch.empty((64, 64), dtype=torch.float64, device=dev)
+        rec = {}
+        for solver in ("persistent", "pcg"):
+            for _ in range(3):
+                sc.solve_biharmonic(f, g, x, prec="f64", solver=solver, rtol=1e-10)
+            ms, info = [], None
+            for _ in range(10):
+                info, t = timed(lambda: sc.solve_biharmonic(f, g, x, prec="f64", solver=solver, rtol=1e-10))
+                ms.append(t)
+            rec[solver] = {"ms_median": statistics.median(ms), "iters": info["iters"], "rel_res": info["rel_res"],
+                           "linf_err_vs_exact": float(np.max(np.abs(x.cpu().numpy() - m["u_exact"])))}
+        out["plate_64"] = rec
+        # Cahn-Hilliard 1024^2, 20 steps
+        n = 1024
+        u0 = manufactured.ch_uniform(n, 2, seed=2205, amp=0.05, batch=1)
+        u = torch.from_numpy(u0).to(dev)
+        c = sc.make_ch((n, n), 1, (1, n), 1e-6, 1.0, 0.01 ** 2, rtol=1e-10)
+        work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
+        m0, _ = sc.ch_stats(c, u)
+        steps = []
+        for k in range(20):
+            infos, t = timed(lambda: sc.ch_step(c, u, work=work))
+            mk, _ = sc.ch_stats(c, u)
+            steps.append({"ms": round(t, 3), "iters": infos[0]["iters"], "rel_res": infos[0]["rel_res"],
+                          "mass_drift_rel": abs(mk[0] - m0[0]) / float(np.abs(u0).sum())})
+            assert infos[0]["status"] == 0 and infos[0]["rel_res"] <= 1e-10
+        out["ch2d_1024"] = {"ms_per_step_median": statistics.median(s_["ms"] for s_ in steps),
+                            "prec": infos[0]["prec"], "steps": steps,
+                            "mass_drift_rel_max": max(s_["mass_drift_rel"] for s_ in steps)}
+        del u, work
+        # Cahn-Hilliard 8 x 256^3, 5 steps, energy per step
+        n, batch = 256, 8
+        u0 = manufactured.ch_uniform(n, 3, seed=2205, amp=0.05, batch=batch)
+        u = torch.from_numpy(u0).to(dev)
+        c = sc.make_ch((n, n, n), batch, (1, n), 1e-6, 1.0, 0.02 ** 2, rtol=1e-10)
+        work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
+        m0, e0 = sc.ch_stats(c, u)
+        energies, steps = [list(e0)], []
+        for k in range(5):
+            infos, t = timed(lambda: sc.ch_step(c, u, work=work))
+            mk, ek = sc.ch_stats(c, u)
+            energies.append(list(ek))
+            steps.append({"ms": round(t, 2), "iters_max": max(i["iters"] for i in infos)})
+            assert all(i["status"] == 0 and i["rel_res"] <= 1e-10 for i in infos)
+        mono = all(energies[k + 1][b] <= energies[k][b] for k in range(5) for b in range(batch))
+        s0 = float(np.abs(u0).sum(axis=(1, 2, 3)).max())
+        out["ch3d_8x256"] = {"ms_per_step_median": statistics.median(s_["ms"] for s_ in steps), "steps": steps,
+                             "prec": infos[0]["prec"], "energy_nonincreasing_every_step_every_field": mono,
+                             "energy_field0": energies and [e[0] for e in energies],
+                             "mass_drift_rel_max": max(abs(a - b) for a, b in zip(m0, mk)) / s0}
+        assert mono
+        del u, work
+        # the paper's spinodal benchmark
+        for nd, n, dt, chunks, per in ((2, 200, 0.05, 20, 100), (3, 64, 0.25, 10, 40)):
+            u0 = manufactured.ch_spinodal_ic(n, nd, float(n))[None]
+            u = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+            c = sc.make_ch((n,) * nd, 1, (n, n), dt, 5.0, 2.0, chem="double_well", rho=5.0, ca=0.3, cb=0.7,
+                           rtol=1e-10)
+            _, e0 = sc.ch_stats(c, u)
+            es, ms_tot, its = [e0[0]], 0.0, []
+            for k in range(chunks):
+                infos, t = timed(lambda: sc.ch_run(c, u, per, use_graph=True))
+                ms_tot += t
+                its.append(max(step[0]["iters"] for step in infos))
+                assert all(step[0]["status"] == 0 and step[0]["rel_res"] <= 1e-10 for step in infos)
+                es.append(sc.ch_stats(c, u)[1][0])
+            mono = all(es[k + 1] <= es[k] for k in range(chunks))
+            out[f"spinodal_{nd}d"] = {"grid": f"{n}^{nd}, h = 1", "dt": dt, "steps": chunks * per,
+                                      "t_final": chunks * per * dt, "ms_per_step": ms_tot / (chunks * per),
+                                      "free_energy": [round(e, 6) for e in es],
+                                      "energy_nonincreasing": mono, "iters_max_per_chunk": its}
+            assert mono
+            del u
+    out["clocks"] = clk.summary()
+    return out
+
+
 def solver_line(args, res, workload):
     sec = res["sec"]
     med = statistics.median(sec)
@@ -807,6 +923,9 @@ def main():
                    "served": r["served"], "plain": r["plain"], "all_converged": r["all_converged"],
                    "preconditioned_requests": r["preconditioned_requests"],
                    "max_rel_diff_linf_error_served_vs_plain": r["max_rel_diff_linf_error_served_vs_plain"]}
+    solver_cfgs = None
+    if rank == 0 and not args.no_solvers:
+        solver_cfgs = run_solver_configs(local)
     if rank == 0:
         line = {"metric": "composed-stencil apply GB/s (algorithmic: read x + write y)",
                 "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -821,7 +940,7 @@ def main():
                            "per_case_ms": {k: round(v["ms"], 4) for k, v in res["per_case"].items()},
                            "hbm_frac_per_case": {k: round(v["gbs"] / hbm, 4) for k, v in res["per_case"].items()}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": res["clocks"],
-                "gpu_launches": res["launches"], "serving": serving}
+                "gpu_launches": res["launches"], "serving": serving, "solver_configs": solver_cfgs}
         print(json.dumps(line))
     return 0
 

@@ -182,6 +182,18 @@ int sc_apply_composed_host(const sc_stencil *s, int32_t dtype, int32_t bc, const
 
 
 
+/* y = outer(m * inner(x)) on a periodic grid: a composition with a pointwise
+ * coefficient between its factors -- the variable-mobility operator
+ * d/dx(M d/dx(d2/dx2 f)) of Sec. 2.2.4 (inner = d/dx composed with d2/dx2,
+ * m = M at the grid points, outer = d/dx), which a fixed composed stencil
+ * cannot express.  With constant m it equals m times sc_apply_composed of
+ * compose(outer, inner).  x, m, y: n^ndim values of dtype (row-major, x
+ * fastest); work_bytes >= n^ndim values (the scaled intermediate).  x, y, m
+ * and work must not overlap (x may equal m).  Asynchronous on `stream`. */
+int sc_apply_varcoef(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, const int64_t *dims,
+                     int64_t h_num, int64_t h_den, const void *m_dev, const void *x_dev, void *y_dev,
+                     void *work_dev, size_t work_bytes, sc_stream_t stream);
+
 /* ---- Autotuner -------------------------------------------------------------- */
 
 typedef enum {
@@ -344,6 +356,21 @@ typedef struct {
 size_t sc_ch_work_bytes(const sc_ch *p);
 int sc_ch_step(const sc_ch *p, double *u_dev, void *work_dev, size_t work_bytes, sc_solve_info *infos,
                sc_stream_t stream);
+
+/* One step of the semi-implicit backward differentiation scheme of order
+ * 1, 2 or 3 (SBDF1-3) for the same splitting: with history u^n, u^(n-1),
+ * u^(n-2) and N(u) = M Lap f'(u),
+ *   (I + g dt M kappa Lap o Lap) u^(n+1) = sum_j al_j u^(n-j) + g dt M Lap sum_j b_j f'(u^(n-j)),
+ * g = 1, 2/3, 6/11; al = (1), (4/3, -1/3), (18/11, -9/11, 2/11); b = (1), (2, -1),
+ * (3, -3, 1).  The paper (Sec. 4.3) uses IMEX schemes of orders one to three
+ * without naming them; SBDF is the standard family of that kind.  u_dev: u^n
+ * in, u^(n+1) out (batch x n^ndim).  hist_dev (order >= 2): order - 1 slices
+ * of batch x n^ndim values, slice 0 = u^(n-1), slice 1 = u^(n-2); on return
+ * they hold u^n and u^(n-1), the history of the next step.  The caller
+ * starts a run with lower orders (or a history of its own).  Same work space
+ * and solver options as sc_ch_step; order 1 is sc_ch_step. */
+int sc_ch_step_sbdf(const sc_ch *p, int32_t order, double *u_dev, double *hist_dev, void *work_dev,
+                    size_t work_bytes, sc_solve_info *info, sc_stream_t stream);
 
 /* nsteps Cahn-Hilliard steps of every field (the same step as sc_ch_step,
  * persistent solver), set up once.  With use_graph != 0 one whole step --

@@ -14,8 +14,8 @@ from .stencil import (Stencil, stencil_1d, stencil_embed, stencil_add, laplacian
                       compose_stencil, stencil_weights, D1_C2, D2_C2, D1_C4, D2_C4, D1_FWD, D2_FWD)
 from .ops import (apply_composed, apply_composed_host, apply_host_work_bytes,  # noqa: F401
                   apply_composition, apply_composition_work_bytes, autotune_apply, apply_tuned, tune_set,
-                  apply_tuned_host, apply_tuned_host_work_bytes,
+                  apply_tuned_host, apply_tuned_host_work_bytes, apply_varcoef,
                   F64, F32, BC_PERIODIC, BC_GHOSTED, BC_ZERO)
 from .solvers import (solve_biharmonic, solve_biharmonic_batch, make_bvp, bvp_work_bytes,  # noqa: F401
-                      make_ch, ch_step, ch_run, ch_stats, ch_work_bytes, SolveInfo, Bvp, Ch)
+                      make_ch, ch_step, ch_step_sbdf, ch_run, ch_stats, ch_work_bytes, SolveInfo, Bvp, Ch)
 from .server import Server, make_ch_request, make_request, request_bytes  # noqa: F401

@@ -324,11 +324,49 @@ int composition_enqueue(const sc_stencil *B, const sc_stencil *A, int dtype, int
   return apply_enqueue(qb, st);
 }
 
+// t *= m (pointwise coefficient between the factors of a composition)
+template <typename T>
+__global__ void k_scale_pointwise(T *__restrict__ t, const T *__restrict__ m, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    t[i] *= m[i];
+}
+
 }  // namespace sc
 
 using namespace sc;
 
 extern "C" {
+
+int sc_apply_varcoef(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, const int64_t *dims,
+                     int64_t h_num, int64_t h_den, const void *m_dev, const void *x_dev, void *y_dev,
+                     void *work_dev, size_t work_bytes, sc_stream_t stream) {
+  if (int rc = validate_apply(outer, dtype, SC_BC_PERIODIC, dims, h_num, h_den)) return rc;
+  if (int rc = validate_apply(inner, dtype, SC_BC_PERIODIC, dims, h_num, h_den)) return rc;
+  if (outer->ndim != inner->ndim) return fail(SC_EINVAL, "outer and inner dimensions differ");
+  if (!m_dev || !x_dev || !y_dev || !work_dev) return fail(SC_EINVAL, "null device pointer");
+  const size_t es = dtype == SC_F64 ? 8 : 4;
+  const long long n = (long long)grid_elems_ext(outer->ndim, dims, 0);
+  if (work_bytes < size_t(n) * es) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, size_t(n) * es);
+  if (int rc = check_disjoint(outer->ndim, SC_BC_PERIODIC, dims, 0, es, x_dev, y_dev, work_dev, size_t(n) * es))
+    return rc;
+  if (spans_overlap(m_dev, size_t(n) * es, work_dev, size_t(n) * es) ||
+      spans_overlap(m_dev, size_t(n) * es, y_dev, size_t(n) * es))
+    return fail(SC_EINVAL, "m must not overlap y or the work space");
+  cudaStream_t st = (cudaStream_t)stream;
+  ApplyReq qa{inner, dtype, SC_BC_PERIODIC, dims, h_num, h_den, x_dev, work_dev};
+  if (int rc = apply_enqueue(qa, st)) return rc;
+  const int g = int(std::min<long long>((n + 255) / 256, 8LL * num_sms()));
+  if (dtype == SC_F64)
+    k_scale_pointwise<double><<<g, 256, 0, st>>>(static_cast<double *>(work_dev), static_cast<const double *>(m_dev), n);
+  else
+    k_scale_pointwise<float><<<g, 256, 0, st>>>(static_cast<float *>(work_dev), static_cast<const float *>(m_dev), n);
+  ApplyReq qb{outer, dtype, SC_BC_PERIODIC, dims, h_num, h_den, work_dev, y_dev};
+  int rc = apply_enqueue(qb, st);
+  if (!rc) clear_error();
+  return rc;
+}
+
 
 int sc_apply_composed(const sc_stencil *s, int32_t dtype, int32_t bc, const int64_t *dims,
                       int64_t h_num, int64_t h_den, const void *x_dev, void *y_dev,

@@ -60,6 +60,35 @@ __global__ void k_fprime(const double *__restrict__ u, double *__restrict__ g, l
   }
 }
 
+// g = sum_j b_j f'(u^(n-j)) over the history (u0 = u^n, h1 = u^(n-1), h2 = u^(n-2))
+__global__ void k_fprime_hist(const double *__restrict__ u0, const double *__restrict__ h1,
+                              const double *__restrict__ h2, int order, double b0, double b1, double b2,
+                              double *__restrict__ g, long long n, int chem, double rho, double ca, double cb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    auto fp = [&](double c) {
+      return chem == 0 ? c * c * c - c : 2.0 * rho * (c - ca) * (c - cb) * (2.0 * c - ca - cb);
+    };
+    double v = b0 * fp(u0[i]);
+    if (order > 1) v += b1 * fp(h1[i]);
+    if (order > 2) v += b2 * fp(h2[i]);
+    g[i] = v;
+  }
+}
+
+// y = sum_j al_j u^(n-j) + c y   (y holds Lap g on entry)
+__global__ void k_sbdf_rhs(double *__restrict__ y, const double *__restrict__ u0, const double *__restrict__ h1,
+                           const double *__restrict__ h2, int order, double a0, double a1, double a2, double c,
+                           long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = a0 * u0[i];
+    if (order > 1) v += a1 * h1[i];
+    if (order > 2) v += a2 * h2[i];
+    y[i] = fma(c, y[i], v);
+  }
+}
+
 // ---- plain CG helpers (one kernel per operation) --------------------------
 constexpr int PL_NTHR = 256;
 constexpr int PL_CHUNK = PL_NTHR * 16;
@@ -1046,6 +1075,47 @@ size_t sc_ch_work_bytes(const sc_ch *c) {
   std::vector<ProbSpec> sps(c->batch);
   for (int i = 0; i < c->batch; ++i) ch_spec(c, i, nullptr, sps[i]);
   return batch_bytes(sps);
+}
+
+int sc_ch_step_sbdf(const sc_ch *c, int32_t order, double *u_dev, double *hist_dev, void *work_dev,
+                    size_t work_bytes, sc_solve_info *infos, sc_stream_t stream) {
+  if (int rc = ch_validate(c)) return rc;
+  if (order < 1 || order > 3) return fail(SC_EINVAL, "order must be 1, 2 or 3");
+  if (!u_dev || !infos || (order > 1 && !hist_dev)) return fail(SC_EINVAL, "null pointer");
+  // SBDF coefficients of the form (I + g dt M kappa B) u+ = sum al_j u^(n-j) + g dt M Lap sum b_j f'
+  static const double AL[4][3] = {{0, 0, 0}, {1, 0, 0}, {4.0 / 3.0, -1.0 / 3.0, 0}, {18.0 / 11.0, -9.0 / 11.0, 2.0 / 11.0}};
+  static const double BE[4][3] = {{0, 0, 0}, {1, 0, 0}, {2, -1, 0}, {3, -3, 1}};
+  static const double GA[4] = {0, 1.0, 2.0 / 3.0, 6.0 / 11.0};
+  const double gdt = GA[order] * c->dt;
+  std::vector<ProbSpec> sps(c->batch);
+  const double h = double(c->h_num) / double(c->h_den);
+  for (int i = 0; i < c->batch; ++i) {
+    ch_spec(c, i, u_dev, sps[i]);
+    sps[i].b = gdt * c->M * c->kappa;
+    const int prec = choose_prec(c->prec, kappa_estimate(sps[i], h));
+    sps[i].mixed = prec == SC_PREC_MIXED && c->solver == SC_SOLVER_PERSISTENT;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long npts = c->n[0] * c->n[1] * (c->ndim == 3 ? c->n[2] : 1);
+  const long long per = npts * c->batch;  // history slice j at hist_dev + (j - 1) * per
+  return solve_set(sps, work_dev, work_bytes, infos, st, [&](int i, SolveProb &P, ProbAux &aux) -> int {
+    const ProbSpec &sp = sps[i];
+    double *u0 = sp.x;
+    double *h1 = order > 1 ? hist_dev + (long long)i * npts : nullptr;
+    double *h2 = order > 2 ? hist_dev + per + (long long)i * npts : nullptr;
+    k_fprime_hist<<<grid1d(npts), 256, 0, st>>>(u0, h1, h2, order, BE[order][0], BE[order][1], BE[order][2],
+                                                aux.scratch, npts, c->chem, c->rho, c->ca, c->cb);
+    sc_stencil L;
+    sc_laplacian(sp.ndim, sp.order, &L);
+    ApplyReq q{&L, SC_F64, SC_BC_PERIODIC, sp.n, sp.h_num, sp.h_den, aux.scratch, P.rhs};
+    if (int rc = apply_enqueue(q, st)) return rc;
+    k_sbdf_rhs<<<grid1d(npts), 256, 0, st>>>(P.rhs, u0, h1, h2, order, AL[order][0], AL[order][1], AL[order][2],
+                                             gdt * c->M, npts);
+    // the history for the next step: u^(n-1) -> slot 2, u^n -> slot 1
+    if (order > 2) cudaMemcpyAsync(h2, h1, size_t(npts) * 8, cudaMemcpyDeviceToDevice, st);
+    if (order > 1) cudaMemcpyAsync(h1, u0, size_t(npts) * 8, cudaMemcpyDeviceToDevice, st);
+    return SC_OK;
+  });
 }
 
 int sc_ch_step(const sc_ch *c, double *u_dev, void *work_dev, size_t work_bytes, sc_solve_info *infos,

@@ -126,6 +126,26 @@ def apply_composition(outer: Stencil, inner: Stencil, x: torch.Tensor, y: torch.
     return y
 
 
+lib.sc_apply_varcoef.argtypes = [_P, _P, ctypes.c_int32, _I64P, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+lib.sc_apply_varcoef.restype = ctypes.c_int
+
+
+def apply_varcoef(outer: Stencil, inner: Stencil, m, x, y, work, h=(1, 1), dims=None, stream=None):
+    """y = outer(m * inner(x)), periodic (the variable-mobility composition)."""
+    require_device("x", x)
+    require_device("y", y, x.dtype)
+    require_device("m", m, x.dtype)
+    require_device("work", work)
+    if dims is None:
+        dims = tuple(reversed(y.shape))
+    check(lib.sc_apply_varcoef(ctypes.byref(outer), ctypes.byref(inner), dtype_code(y.dtype), dims_arg(dims),
+                               int(h[0]), int(h[1]), ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                               ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                               work.numel() * work.element_size(), stream_arg(stream)))
+    return y
+
+
 EVAL_NAMES = {0: "flat", 1: "nested", 2: "pair", 3: "fused"}
 
 

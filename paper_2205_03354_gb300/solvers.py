@@ -155,6 +155,26 @@ def ch_step(c: Ch, u: torch.Tensor, work=None, stream=None) -> list:
     return [i.as_dict() for i in infos]
 
 
+lib.sc_ch_step_sbdf.argtypes = [_CP, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_size_t, _IP, ctypes.c_void_p]
+lib.sc_ch_step_sbdf.restype = ctypes.c_int
+
+
+def ch_step_sbdf(c: Ch, u: torch.Tensor, hist, order: int, work=None, stream=None) -> list:
+    """One SBDF step of the given order (1-3): u (u^n) in place -> u^(n+1);
+    hist (order >= 2: (order - 1) x batch x n^d) -> the next step's history."""
+    require_device("u", u, torch.float64)
+    if order > 1:
+        require_device("hist", hist, torch.float64)
+    nb = ch_work_bytes(c)
+    w = _work(nb, u.device, work)
+    infos = (SolveInfo * c.batch)()
+    check(lib.sc_ch_step_sbdf(ctypes.byref(c), int(order), ctypes.c_void_p(u.data_ptr()),
+                              ctypes.c_void_p(hist.data_ptr() if order > 1 else 0), ctypes.c_void_p(w.data_ptr()),
+                              nb, infos, stream_arg(stream)))
+    return [i.as_dict() for i in infos]
+
+
 def ch_stats(c: Ch, u: torch.Tensor, work=None, stream=None):
     """(mass[batch], energy[batch]) as Python lists."""
     require_device("u", u, torch.float64)

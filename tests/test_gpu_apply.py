@@ -489,3 +489,64 @@ def test_pair_arithmetic_wide_dynamic_range(ndim, dims, bc):
     torch.cuda.synchronize()
     _nested_check(L, oL, x, yt, bc, n, 2.0 ** -42)
     assert not torch.equal(yt, yn)
+
+
+def _mobility_factors(ndim, axis=0):
+    """d/dx and d/dx composed with d2/dx2, along one axis (library and oracle)."""
+    d1 = sc.stencil_embed(sc.stencil_1d(sc.D1_C2), ndim, axis)
+    d2 = sc.stencil_embed(sc.stencil_1d(sc.D2_C2), ndim, axis)
+    o1 = ost.embed(ost.d1_central2(), ndim, axis)
+    o2 = ost.embed(ost.d2_central2(), ndim, axis)
+    return d1, sc.compose_stencil(d1, d2), o1, ost.compose(o1, o2)
+
+
+@pytest.mark.parametrize("ndim,dims,axis", [(2, (130, 70), 0), (2, (96, 64), 1), (3, (40, 30, 20), 2)])
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_varcoef_apply_matches_oracle(ndim, dims, axis, dt):
+    """d/dx(M d/dx(d2/dx2 x)) with a random positive mobility M (Sec. 2.2.4)
+    against the oracle's definition, elementwise within the rounding of two
+    short sums and one product."""
+    outer, inner, oo, oi = _mobility_factors(ndim, axis)
+    n = dims[0]
+    shape = tuple(reversed(dims))
+    rng = np.random.default_rng(ndim * 10 + axis)
+    x = rng.uniform(-1, 1, shape).astype(dt)
+    m = rng.uniform(0.5, 2.0, shape).astype(dt)
+    xt, mt = torch.from_numpy(x).to(DEV), torch.from_numpy(m).to(DEV)
+    yt = torch.full(shape, float("nan"), dtype=xt.dtype, device=DEV)
+    work = torch.empty(x.size * x.itemsize, dtype=torch.uint8, device=DEV)
+    sc.apply_varcoef(outer, inner, mt, xt, yt, work, h=(1, n), dims=dims)
+    torch.cuda.synchronize()
+    wo = oracle_weights(oo, Fraction(1, n), dt)
+    wi = oracle_weights(oi, Fraction(1, n), dt)
+    ref = oap.apply_varcoef(wo, wi, m.astype(np.float64), x.astype(np.float64))
+    ao = {k: abs(float(v)) for k, v in wo.items()}
+    ai = {k: abs(float(v)) for k, v in wi.items()}
+    mag = oap.apply_varcoef(ao, ai, np.abs(m.astype(np.float64)), np.abs(x.astype(np.float64)))
+    tol = (oo.npts + oi.npts + 2) * np.finfo(dt).eps * mag
+    err = np.abs(yt.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= tol), float(np.max(err / (mag + 1e-300)))
+
+
+def test_varcoef_explicit_stability_limit():
+    """Explicit Euler steps of f_t = -d/dx(M d/dx(d2/dx2 f)) with M = 1 through
+    the composed operator (Sec. 2.2.4, Table 1): stable at 0.98 x (27/32) h^4,
+    unstable at 1.05 x (27/32) h^4 (the worst mode grows by |1 - 2.1| per step)."""
+    n = 256
+    outer, inner, _, _ = _mobility_factors(2, 0)
+    rng = np.random.default_rng(3)
+    u0 = torch.from_numpy(rng.uniform(-1, 1, (4, n))).to(DEV)
+    m = torch.ones_like(u0)
+    y = torch.empty_like(u0)
+    work = torch.empty(u0.numel() * 8, dtype=torch.uint8, device=DEV)
+    h4 = (1.0 / n) ** 4
+    growth = {}
+    for fac in (0.98, 1.05):
+        u = u0.clone()
+        dt = fac * 27.0 / 32.0 * h4
+        for _ in range(300):
+            sc.apply_varcoef(outer, inner, m, u, y, work, h=(1, n))
+            u -= dt * y
+        growth[fac] = float(u.abs().max() / u0.abs().max())
+    assert growth[0.98] <= 1.0 + 1e-9, growth
+    assert growth[1.05] > 100.0, growth
