@@ -669,6 +669,7 @@ def run_solver_configs(local):
         u = torch.from_numpy(u0).to(dev)
         c = sc.make_ch((n, n), 1, (1, n), 1e-6, 1.0, 0.01 ** 2, rtol=1e-10)
         work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
+        tun2 = sc.autotune_ch(c, torch.from_numpy(u0.copy()).to(dev), iters=100, work=work)
         m0, _ = sc.ch_stats(c, u)
         steps = []
         for k in range(20):
@@ -677,7 +678,7 @@ def run_solver_configs(local):
             steps.append({"ms": round(t, 3), "iters": infos[0]["iters"], "rel_res": infos[0]["rel_res"],
                           "mass_drift_rel": abs(mk[0] - m0[0]) / float(np.abs(u0).sum())})
             assert infos[0]["status"] == 0 and infos[0]["rel_res"] <= 1e-10
-        out["ch2d_1024"] = {"ms_per_step_median": statistics.median(s_["ms"] for s_ in steps),
+        out["ch2d_1024"] = {"ms_per_step_median": statistics.median(s_["ms"] for s_ in steps), "solver_tuning": tun2,
                             "prec": infos[0]["prec"], "steps": steps,
                             "mass_drift_rel_max": max(s_["mass_drift_rel"] for s_ in steps)}
         del u, work
@@ -687,6 +688,7 @@ def run_solver_configs(local):
         u = torch.from_numpy(u0).to(dev)
         c = sc.make_ch((n, n, n), batch, (1, n), 1e-6, 1.0, 0.02 ** 2, rtol=1e-10)
         work = torch.empty(sc.ch_work_bytes(c), dtype=torch.uint8, device=dev)
+        tun3 = sc.autotune_ch(c, torch.from_numpy(u0.copy()).to(dev), iters=40, work=work)
         m0, e0 = sc.ch_stats(c, u)
         energies, steps = [list(e0)], []
         for k in range(5):
@@ -698,6 +700,7 @@ def run_solver_configs(local):
         mono = all(energies[k + 1][b] <= energies[k][b] for k in range(5) for b in range(batch))
         s0 = float(np.abs(u0).sum(axis=(1, 2, 3)).max())
         out["ch3d_8x256"] = {"ms_per_step_median": statistics.median(s_["ms"] for s_ in steps), "steps": steps,
+                             "solver_tuning": tun3,
                              "prec": infos[0]["prec"], "energy_nonincreasing_every_step_every_field": mono,
                              "energy_field0": energies and [e[0] for e in energies],
                              "mass_drift_rel_max": max(abs(a - b) for a, b in zip(m0, mk)) / s0}

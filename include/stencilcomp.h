@@ -414,6 +414,34 @@ int sc_ch_stats_noalloc(const sc_ch *p, const double *u_dev, double *mass_host, 
 void sc_noalloc_forget(void);
 
 
+/* ---- Autotuner of the persistent solver ------------------------------------ */
+
+/* The persistent engine cuts every problem into tiles of about a target
+ * number of points (FP32: 1024 in 2D, 2048 in 3D; FP64 4x fewer), which sets
+ * both the tile count per problem (the work a CTA group shares) and the
+ * planes a tile streams (its halo-blocking depth).  The target is scaled by
+ * 2^log2_scale, log2_scale in -2..2, separately for each (dimensionality,
+ * precision class); default 0.  sc_autotune_solver times `iters` inner
+ * iterations of the caller's batch (plate problems; their x is overwritten)
+ * at every scale on `stream`, keeps the fastest for the classes present in
+ * the batch (process-wide, later solves and server slices use it) and
+ * reports the times.  Synchronous.  A problem's results depend on the scale
+ * it was laid out with (the reduction groups follow the tiles) and on nothing
+ * else: the same scale gives the same bits.  work_bytes as for
+ * sc_solve_biharmonic_batch, which already covers every scale. */
+typedef struct {
+  int32_t log2_scale;  /* the chosen scale                                 */
+  float ms[5];         /* time of the timed iterations at scales -2 .. 2   */
+} sc_solver_tuning;
+int sc_autotune_solver(const sc_bvp *probs, int32_t count, int32_t iters, void *work_dev, size_t work_bytes,
+                       sc_solver_tuning *out, sc_stream_t stream);
+/* The same for a batch of Cahn-Hilliard steps (u is advanced partly). */
+int sc_autotune_ch(const sc_ch *p, double *u_dev, int32_t iters, void *work_dev, size_t work_bytes,
+                   sc_solver_tuning *out, sc_stream_t stream);
+/* Set / read the scale of one class (prec: SC_PREC_F64 or SC_PREC_MIXED). */
+int sc_solver_tile_scale_set(int32_t ndim, int32_t prec, int32_t log2_scale);
+int sc_solver_tile_scale_get(int32_t ndim, int32_t prec, int32_t *log2_scale);
+
 /* Failure-detection self-test of the solver's bounded group barrier: runs
  * the barrier for a group of two CTAs with only one launched, so the release
  * never comes, once with each reduction protocol (every CTA reading the

@@ -17,5 +17,6 @@ from .ops import (apply_composed, apply_composed_host, apply_host_work_bytes,  #
                   apply_tuned_host, apply_tuned_host_work_bytes, apply_varcoef,
                   F64, F32, BC_PERIODIC, BC_GHOSTED, BC_ZERO)
 from .solvers import (solve_biharmonic, solve_biharmonic_batch, make_bvp, bvp_work_bytes,  # noqa: F401
-                      make_ch, ch_step, ch_step_sbdf, ch_run, ch_stats, ch_work_bytes, SolveInfo, Bvp, Ch)
+                      make_ch, ch_step, ch_step_sbdf, ch_run, ch_stats, ch_work_bytes, SolveInfo, Bvp, Ch,
+                      autotune_solver, autotune_ch, solver_tile_scale_set, solver_tile_scale_get)
 from .server import Server, make_ch_request, make_request, request_bytes  # noqa: F401

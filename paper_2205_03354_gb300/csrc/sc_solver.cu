@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -197,8 +198,18 @@ __global__ void k_ch_stats_part(const double *__restrict__ u, int ndim, int nx, 
 
 
 
+// Tile-size scale of the persistent solver per (ndim, precision class):
+// the tile targets below are multiplied by it.  Set by sc_autotune_solver or
+// sc_solver_tile_scale_set; 1 by default.  Stored as the scale's log2 + 8.
+static std::atomic<int> g_tile_log2[2][2] = {{{8}, {8}}, {{8}, {8}}};
+constexpr int TILE_LOG2_MIN = -2, TILE_LOG2_MAX = 2;  // scales 1/4 .. 4
+
+static double tile_scale(int ndim, bool mixed) {
+  return std::ldexp(1.0, g_tile_log2[ndim == 3][mixed ? 1 : 0].load(std::memory_order_relaxed) - 8);
+}
+
 template <typename T, int NDIM, int R>
-static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
+static void tiles_for(const ProbSpec &sp, int &H, int &ntiles, double scale = -1.0) {
   using K = FlatApply<T, NDIM, R, CLS_CROSS2, 1>;
   const long long nx = sp.n[0], ny = sp.n[1], nz = NDIM == 3 ? sp.n[2] : 1;
   const long long txy = ((nx + K::BX - 1) / K::BX) * (NDIM == 3 ? (ny + K::BY - 1) / K::BY : 1);
@@ -209,7 +220,9 @@ static void tiles_for(const ProbSpec &sp, int &H, int &ntiles) {
   // 1024 points (short row streams keep small grids parallel), at most one
   // round of the CTAs a 2D launch keeps resident (4 per SM).  FP64 tiles
   // are 4x smaller: a warp retires one FP64 FMA instruction per 64 clocks
-  const long long per = (NDIM == 3 ? 2048 : 1024) / (sizeof(T) == 8 ? 4 : 1);
+  if (scale <= 0.0) scale = tile_scale(NDIM, sp.mixed);
+  const long long per =
+      std::max<long long>(16, (long long)((NDIM == 3 ? 2048 : 1024) / (sizeof(T) == 8 ? 4 : 1) * scale));
   const long long target =
       NDIM == 3 ? std::max<long long>(1, std::min<long long>(npts / per, 1024))
                 : std::max<long long>(1, std::min<long long>(npts / per, 4LL * num_sms()));
@@ -254,8 +267,26 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
   P.chunk = CG_STEP;
   while ((npts + P.chunk - 1) / P.chunk > 1024) P.chunk *= 2;
   P.nchunks = int((npts + P.chunk - 1) / P.chunk);
-  // the plain path reduces in blocks of PL_CHUNK points through the same slots
-  P.nslot = std::max({P.ntiles_in, P.ntiles_64, P.nchunks, int((npts + 4095) / 4096)});
+  // the plain path reduces in blocks of PL_CHUNK points through the same slots;
+  // the slots also cover the most tiles any tile scale gives, so that a work
+  // space sized once serves every tuning choice
+  int most = 0;
+  {
+    int hh, nt;
+    const double smin = std::ldexp(1.0, TILE_LOG2_MIN);
+    if (sp.ndim == 2) {
+      tiles_for<float, 2, 2>(sp, hh, nt, smin);
+      most = std::max(most, nt);
+      tiles_for<double, 2, 2>(sp, hh, nt, smin);
+      most = std::max(most, nt);
+    } else {
+      tiles_for<float, 3, 2>(sp, hh, nt, smin);
+      most = std::max(most, nt);
+      tiles_for<double, 3, 2>(sp, hh, nt, smin);
+      most = std::max(most, nt);
+    }
+  }
+  P.nslot = std::max({P.ntiles_in, P.ntiles_64, P.nchunks, int((npts + 4095) / 4096), most});
   P.a = sp.a;
   P.b = sp.b;
   P.mixed = sp.mixed;
@@ -891,6 +922,77 @@ __global__ void k_barrier_timeout_probe(SolveProb *P, long long spin_limit) {
   if (threadIdx.x == 0) P->st->status = (!ok_small && !ok_publish) ? SC_ETIMEOUT : SC_OK;
 }
 
+// Times `iters` inner iterations of the persistent engine on the problem
+// set for every tile scale and keeps the fastest for the classes present.
+template <class SETUP>
+static int tune_solver_set(std::vector<ProbSpec> &sps, void *work, size_t work_bytes, int iters, cudaStream_t st,
+                           SETUP setup, sc_solver_tuning *out) {
+  if (!work) return fail(SC_EINVAL, "null work space");
+  if (iters < 1 || iters > 100000) return fail(SC_EINVAL, "iters must be 1..100000");
+  for (const ProbSpec &sp : sps)
+    if (sp.solver != SC_SOLVER_PERSISTENT) return fail(SC_EINVAL, "the tuner times the persistent solver");
+  const size_t need = batch_bytes(sps);
+  if (work_bytes < need) return fail(SC_ENOMEM, "work space %zu < %zu bytes", work_bytes, need);
+  bool cls[2][2] = {{false, false}, {false, false}};
+  for (const ProbSpec &sp : sps) cls[sp.ndim == 3][sp.mixed ? 1 : 0] = true;
+  int saved[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) saved[a][b] = g_tile_log2[a][b].load();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_ms = 1e300;
+  int best = 0;
+  std::memset(out, 0, sizeof(*out));
+  for (int lg = TILE_LOG2_MIN; lg <= TILE_LOG2_MAX; ++lg) {
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        if (cls[a][b]) g_tile_log2[a][b].store(lg + 8);
+    Carver cv(work, work_bytes);
+    std::vector<SolveProb> hp(sps.size());
+    std::vector<ProbAux> aux(sps.size());
+    for (size_t i = 0; i < sps.size(); ++i) {
+      layout(sps[i], cv, hp[i], aux[i]);
+      aux[i].ones = static_cast<double *>(cv.take(std::max<long long>(hp[i].npts, 1) * 8));
+    }
+    SolveProb *dprobs = static_cast<SolveProb *>(cv.take(sps.size() * sizeof(SolveProb)));
+    int *dmap = static_cast<int *>(cv.take(sizeof(int) * size_t(32) * num_sms()));
+    unsigned *dbars = static_cast<unsigned *>(cv.take(sps.size() * 2 * sizeof(unsigned)));
+    int rc = SC_OK;
+    for (size_t i = 0; i < sps.size() && !rc; ++i) {
+      rc = upload_prob(sps[i], hp[i], aux[i], st);
+      if (!rc) rc = setup(int(i), hp[i], aux[i]);
+    }
+    float ms = 0.0f;
+    if (!rc) {
+      cudaEventRecord(e0, st);
+      rc = run_persistent(hp, dprobs, dmap, dbars, st, iters, 0.0);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (rc) {
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) g_tile_log2[a][b].store(saved[a][b]);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+    out->ms[lg - TILE_LOG2_MIN] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = lg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) g_tile_log2[a][b].store(cls[a][b] ? best + 8 : saved[a][b]);
+  out->log2_scale = best;
+  clear_error();
+  return SC_OK;
+}
+
 }  // namespace sc
 
 using namespace sc;
@@ -1053,6 +1155,47 @@ size_t sc_bvp_batch_work_bytes(const sc_bvp *probs, int32_t count) {
 }
 
 size_t sc_bvp_work_bytes(const sc_bvp *p) { return sc_bvp_batch_work_bytes(p, 1); }
+
+int sc_autotune_solver(const sc_bvp *probs, int32_t count, int32_t iters, void *work_dev, size_t work_bytes,
+                       sc_solver_tuning *out, sc_stream_t stream) {
+  if (!probs || count < 1 || !out) return fail(SC_EINVAL, "bad arguments");
+  std::vector<ProbSpec> sps(count);
+  for (int i = 0; i < count; ++i)
+    if (int rc = bvp_spec(&probs[i], sps[i])) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return tune_solver_set(sps, work_dev, work_bytes, iters, st, [&](int i, SolveProb &P, ProbAux &aux) {
+    return setup_bvp(&probs[i], sps[i], P, aux, st);
+  }, out);
+}
+
+int sc_autotune_ch(const sc_ch *c, double *u_dev, int32_t iters, void *work_dev, size_t work_bytes,
+                   sc_solver_tuning *out, sc_stream_t stream) {
+  if (int rc = ch_validate(c)) return rc;
+  if (!u_dev || !out) return fail(SC_EINVAL, "null pointer");
+  std::vector<ProbSpec> sps(c->batch);
+  for (int i = 0; i < c->batch; ++i) ch_spec(c, i, u_dev, sps[i]);
+  cudaStream_t st = (cudaStream_t)stream;
+  return tune_solver_set(sps, work_dev, work_bytes, iters, st, [&](int i, SolveProb &P, ProbAux &aux) {
+    return setup_ch(c, sps[i], P, aux, st);
+  }, out);
+}
+
+int sc_solver_tile_scale_set(int32_t ndim, int32_t prec, int32_t log2_scale) {
+  if (ndim != 2 && ndim != 3) return fail(SC_EINVAL, "ndim must be 2 or 3");
+  if (prec != SC_PREC_F64 && prec != SC_PREC_MIXED) return fail(SC_EINVAL, "prec must be F64 or MIXED");
+  if (log2_scale < TILE_LOG2_MIN || log2_scale > TILE_LOG2_MAX) return fail(SC_EINVAL, "log2_scale out of range");
+  g_tile_log2[ndim == 3][prec == SC_PREC_MIXED].store(log2_scale + 8);
+  clear_error();
+  return SC_OK;
+}
+
+int sc_solver_tile_scale_get(int32_t ndim, int32_t prec, int32_t *log2_scale) {
+  if ((ndim != 2 && ndim != 3) || (prec != SC_PREC_F64 && prec != SC_PREC_MIXED) || !log2_scale)
+    return fail(SC_EINVAL, "bad arguments");
+  *log2_scale = g_tile_log2[ndim == 3][prec == SC_PREC_MIXED].load() - 8;
+  clear_error();
+  return SC_OK;
+}
 
 int sc_solve_biharmonic_batch(const sc_bvp *probs, int32_t count, void *work_dev, size_t work_bytes,
                               sc_solve_info *infos, sc_stream_t stream) {

@@ -247,3 +247,54 @@ def selftest_barrier_timeout(spin_limit: int = 1 << 14, stream=None) -> int:
     check(lib.sc_selftest_barrier_timeout(ctypes.c_void_p(w.data_ptr()), 4096, spin_limit, ctypes.byref(st),
                                           stream_arg(stream)))
     return st.value
+
+
+class SolverTuning(ctypes.Structure):
+    _fields_ = [("log2_scale", ctypes.c_int32), ("ms", ctypes.c_float * 5)]
+
+    def as_dict(self):
+        return {"log2_scale": int(self.log2_scale), "ms_by_log2_scale": {k - 2: float(self.ms[k]) for k in range(5)}}
+
+
+lib.sc_autotune_solver.argtypes = [_BP, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.POINTER(SolverTuning), ctypes.c_void_p]
+lib.sc_autotune_solver.restype = ctypes.c_int
+lib.sc_autotune_ch.argtypes = [_CP, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                               ctypes.POINTER(SolverTuning), ctypes.c_void_p]
+lib.sc_autotune_ch.restype = ctypes.c_int
+lib.sc_solver_tile_scale_set.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+lib.sc_solver_tile_scale_set.restype = ctypes.c_int
+lib.sc_solver_tile_scale_get.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+lib.sc_solver_tile_scale_get.restype = ctypes.c_int
+
+
+def autotune_solver(probs: list, iters: int = 200, work=None, stream=None) -> dict:
+    """Times the persistent engine's tile scales on a plate batch (x buffers
+    are overwritten) and keeps the fastest for the classes present."""
+    arr = (Bvp * len(probs))(*probs)
+    nb = int(lib.sc_bvp_batch_work_bytes(arr, len(probs)))
+    w = _work(nb, torch.device("cuda", torch.cuda.current_device()), work)
+    t = SolverTuning()
+    check(lib.sc_autotune_solver(arr, len(probs), iters, ctypes.c_void_p(w.data_ptr()), nb, ctypes.byref(t),
+                                 stream_arg(stream)))
+    return t.as_dict()
+
+
+def autotune_ch(c: Ch, u: torch.Tensor, iters: int = 100, work=None, stream=None) -> dict:
+    require_device("u", u, torch.float64)
+    nb = ch_work_bytes(c)
+    w = _work(nb, u.device, work)
+    t = SolverTuning()
+    check(lib.sc_autotune_ch(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), iters, ctypes.c_void_p(w.data_ptr()),
+                             nb, ctypes.byref(t), stream_arg(stream)))
+    return t.as_dict()
+
+
+def solver_tile_scale_set(ndim: int, prec: str, log2_scale: int) -> None:
+    check(lib.sc_solver_tile_scale_set(ndim, _PREC[prec], log2_scale))
+
+
+def solver_tile_scale_get(ndim: int, prec: str) -> int:
+    v = ctypes.c_int32()
+    check(lib.sc_solver_tile_scale_get(ndim, _PREC[prec], ctypes.byref(v)))
+    return int(v.value)

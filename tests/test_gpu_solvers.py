@@ -435,3 +435,41 @@ def test_sbdf_temporal_convergence_on_the_spinodal_problem():
         rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
         print(f"SBDF{order}: errors {errs} rates {rates}")
         assert all(abs(r - order) <= 0.35 for r in rates), (order, errs, rates)
+
+
+def test_solver_autotuner_times_every_scale_and_results_follow_the_scale():
+    """sc_autotune_solver times the persistent engine at tile scales 1/4..4 on
+    a plate batch and keeps the fastest; solves then converge at every scale,
+    the same scale gives the same bits, and results of different scales
+    agree within what the 1e-10 residual allows."""
+    specs = [(40, 2, "f64"), (33, 2, "mixed"), (14, 3, "f64"), (64, 2, "f64")]
+    inputs = [bvp_inputs(n, nd, ks=(1, 2, 1)[:nd]) for n, nd, _ in specs]
+    saved = {(nd, p): sc.solver_tile_scale_get(nd, p) for nd in (2, 3) for p in ("f64", "mixed")}
+    try:
+        probs = [sc.make_bvp(f, g, x, prec=p, rtol=RTOL) for (m, f, g, x), (_, _, p) in zip(inputs, specs)]
+        tun = sc.autotune_solver(probs, iters=100)
+        assert -2 <= tun["log2_scale"] <= 2 and all(v > 0 for v in tun["ms_by_log2_scale"].values()), tun
+        print("solver tuning", tun)
+        results = {}
+        for lg in (-2, 0, 2, tun["log2_scale"]):
+            for nd in (2, 3):
+                for p in ("f64", "mixed"):
+                    sc.solver_tile_scale_set(nd, p, lg)
+            outs = []
+            for rep in range(2):
+                xs = [torch.full_like(x, np.nan) for (m, f, g, x) in inputs]
+                probs = [sc.make_bvp(f, g, x2, prec=p, rtol=RTOL)
+                         for (m, f, g, x), x2, (_, _, p) in zip(inputs, xs, specs)]
+                infos = sc.solve_biharmonic_batch(probs)
+                assert all(i["status"] == 0 and i["rel_res"] <= RTOL for i in infos), (lg, infos)
+                outs.append([x2.cpu().numpy() for x2 in xs])
+            assert all(np.array_equal(a, b) for a, b in zip(outs[0], outs[1])), lg
+            results[lg] = outs[0]
+        for k, ((m, f, g, x), (n, nd, p)) in enumerate(zip(inputs, specs)):
+            ref = results[0][k]
+            for lg in (-2, 2):
+                rel = np.linalg.norm(results[lg][k] - ref) / np.linalg.norm(ref)
+                assert rel <= 2 * kappa_bvp(n, nd) * RTOL, (lg, k, rel)
+    finally:
+        for (nd, p), v in saved.items():
+            sc.solver_tile_scale_set(nd, p, v)
