@@ -67,7 +67,7 @@ typedef enum { SC_BC_PERIODIC = 0, SC_BC_GHOSTED = 1, SC_BC_ZERO = 2 } sc_bc;
 typedef enum {
   SC_D1_C2 = 0,  /* (f_1 - f_-1)/(2h),           Sec. 2.1.1, Eq. f'stencil      */
   SC_D2_C2 = 1,  /* [1,-2,1]/h^2,                Sec. 2.1.2                    */
-  SC_D1_C4 = 2,  /* (8f_1 - f_2 + f_-2 - 8f_-1)/(12h), Sec. 2.2.3, Eq. 4orderf' */
+  SC_D1_C4 = 2,  /* (8f_1 - f_2 + f_-2 - 8f_-1)/(12h), Sec. 2.2.2, Eq. 4orderf' */
   SC_D2_C4 = 3,  /* [-1,16,-30,16,-1]/(12h^2),   the fourth-order 2nd derivative
                     composed in Sec. 3.2                                       */
   SC_D1_FWD = 4, /* (f_1 - f_0)/h,               Sec. 2.2.1                    */
@@ -184,7 +184,7 @@ int sc_apply_composed_host(const sc_stencil *s, int32_t dtype, int32_t bc, const
 
 /* y = outer(m * inner(x)) on a periodic grid: a composition with a pointwise
  * coefficient between its factors -- the variable-mobility operator
- * d/dx(M d/dx(d2/dx2 f)) of Sec. 2.2.4 (inner = d/dx composed with d2/dx2,
+ * d/dx(M d/dx(d2/dx2 f)) of Sec. 2.2.3 (inner = d/dx composed with d2/dx2,
  * m = M at the grid points, outer = d/dx), which a fixed composed stencil
  * cannot express.  With constant m it equals m times sc_apply_composed of
  * compose(outer, inner).  x, m, y: n^ndim values of dtype (row-major, x

@@ -18,7 +18,7 @@ cg         textbook conjugate gradients in FP64.
 bvp        the biharmonic boundary-value problem of Sec. 3.3.
 ch         one semi-implicit Cahn-Hilliard step (Sec. 4, Eq. cahn), mass and
            free energy, and the DFT closed form of a periodic step.
-stability  von Neumann growth factors of Sec. 2.2.4 and Appendix B.
+stability  von Neumann growth factors of Sec. 2.2.3 and Appendix B.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against values the paper prints, closed forms,

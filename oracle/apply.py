@@ -123,7 +123,7 @@ def apply_at(weights: dict, x: np.ndarray, bc: str, points: np.ndarray, radius: 
 
 def apply_varcoef(outer: dict, inner: dict, m: np.ndarray, x: np.ndarray) -> np.ndarray:
     """y = outer(m * inner(x)) on a periodic grid: the composition of Sec.
-    2.2.4 with a pointwise coefficient between the factors (the variable
+    2.2.3 with a pointwise coefficient between the factors (the variable
     mobility of d/dx(M d/dx(d2/dx2 f)): compose d/dx with d2/dx2, scale by M
     at each grid point, compose the result with d/dx)."""
     t = apply(inner, x, "periodic")

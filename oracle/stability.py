@@ -1,5 +1,5 @@
 """von Neumann stability of explicit steps with composed stencils
-(Sec. 2.2.4 and Appendix B).
+(Sec. 2.2.3 and Appendix B).
 
 Oracle (test infrastructure only; see ``oracle/__init__.py``).
 

@@ -73,7 +73,7 @@ def d2_central2() -> Stencil:
 
 
 def d1_central4() -> Stencil:
-    """(8 f_1 - f_2 + f_-2 - 8 f_-1) / (12h): Sec. 2.2.3, Eq. 4orderf'."""
+    """(8 f_1 - f_2 + f_-2 - 8 f_-1) / (12h): Sec. 2.2.2, Eq. 4orderf'."""
     return Stencil.make({(1,): Fraction(8, 12), (2,): Fraction(-1, 12),
                          (-2,): Fraction(1, 12), (-1,): Fraction(-8, 12)}, 1)
 

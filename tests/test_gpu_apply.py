@@ -503,7 +503,7 @@ def _mobility_factors(ndim, axis=0):
 @pytest.mark.parametrize("ndim,dims,axis", [(2, (130, 70), 0), (2, (96, 64), 1), (3, (40, 30, 20), 2)])
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_varcoef_apply_matches_oracle(ndim, dims, axis, dt):
-    """d/dx(M d/dx(d2/dx2 x)) with a random positive mobility M (Sec. 2.2.4)
+    """d/dx(M d/dx(d2/dx2 x)) with a random positive mobility M (Sec. 2.2.3)
     against the oracle's definition, elementwise within the rounding of two
     short sums and one product."""
     outer, inner, oo, oi = _mobility_factors(ndim, axis)
@@ -530,7 +530,7 @@ def test_varcoef_apply_matches_oracle(ndim, dims, axis, dt):
 
 def test_varcoef_explicit_stability_limit():
     """Explicit Euler steps of f_t = -d/dx(M d/dx(d2/dx2 f)) with M = 1 through
-    the composed operator (Sec. 2.2.4, Table 1): stable at 0.98 x (27/32) h^4,
+    the composed operator (Sec. 2.2.3, Table 1): stable at 0.98 x (27/32) h^4,
     unstable at 1.05 x (27/32) h^4 (the worst mode grows by |1 - 2.1| per step)."""
     n = 256
     outer, inner, _, _ = _mobility_factors(2, 0)

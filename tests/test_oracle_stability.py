@@ -1,4 +1,4 @@
-"""Pins of the von Neumann stability constants (Sec. 2.2.4, Table 1,
+"""Pins of the von Neumann stability constants (Sec. 2.2.3, Table 1,
 Appendix B)."""
 import numpy as np
 
