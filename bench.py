@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--nreq", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--n2d", default="32,2048", help="serving: 2D interior size range (log-uniform)")
     ap.add_argument("--n3d", default="32,256", help="serving: 3D interior size range (log-uniform)")
+    ap.add_argument("--ch-frac", dest="ch_frac", type=float, default=0.0,
+                    help="serving: fraction of Cahn-Hilliard step requests in the trace")
     ap.add_argument("--pcg-min", dest="pcg_min", type=int, default=1 << 16,
                     help="serving: plate grids from this many points use the preconditioned solver")
     ap.add_argument("--load", type=float, default=0.7, help="serving: offered load vs plain-path capacity")
@@ -504,9 +506,19 @@ def run_serving(args, local):
     lo2, hi2 = (int(v) for v in args.n2d.split(","))
     lo3, hi3 = (int(v) for v in args.n3d.split(","))
     pcg_min = int(getattr(args, "pcg_min", 1 << 16))
-    tr = requests.trace(args.nreq, seed=2205, rate_per_s=1.0, n2d=(lo2, hi2), n3d=(lo3, hi3))
+    ch_frac = float(getattr(args, "ch_frac", 0.0))
+    tr = requests.trace(args.nreq, seed=2205, rate_per_s=1.0, n2d=(lo2, hi2), n3d=(lo3, hi3), ch_frac=ch_frac)
+    # Cahn-Hilliard step requests: eps 0.01 (2D) / 0.02 (3D), dt 1e-6, u0
+    # uniform in [-0.05, 0.05] from the request's id, h = 1/n, cubic f
+    CH_DT = 1e-6
+
+    def ch_kappa(q):
+        return (0.01 if q["ndim"] == 2 else 0.02) ** 2
 
     def make(q):
+        if q["kind"] == "ch":
+            u0 = manufactured.ch_uniform(q["n"], q["ndim"], seed=10000 + q["id"], amp=0.05)
+            return u0, None, None
         m = manufactured.bvp_case_separable(q["n"], q["ndim"], 2, q["ks"])
         return m["g"], m["u_padded"], m["u_exact"]
 
@@ -514,18 +526,30 @@ def run_serving(args, local):
     dur, err_plain, iters_plain = [], [], []
     for q in tr:
         f, g, ue = make(q)
-        solver = "pcg" if f.size >= pcg_min else "plain"
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ft, gt = torch.from_numpy(f).to(dev), torch.from_numpy(g).to(dev)
-        x = torch.empty(f.shape, dtype=torch.float64, device=dev)
-        info = sc.solve_biharmonic(ft, gt, x, prec="f64", solver=solver, rtol=1e-10)
-        xh = x.cpu().numpy()
-        dur.append(time.perf_counter() - t0)
+        if q["kind"] == "ch":
+            u = torch.from_numpy(f).to(dev).reshape((1,) + f.shape)
+            n_ = q["n"]
+            c = sc.make_ch((n_,) * q["ndim"], 1, (1, n_), CH_DT, 1.0, ch_kappa(q), prec="f64", solver="plain",
+                           rtol=1e-10)
+            info = sc.ch_step(c, u)[0]
+            xh = u.cpu().numpy()[0]
+            dur.append(time.perf_counter() - t0)
+            err_plain.append(float(np.linalg.norm(xh)))  # compared with the served result's norm
+            del u
+        else:
+            solver = "pcg" if f.size >= pcg_min else "plain"
+            ft, gt = torch.from_numpy(f).to(dev), torch.from_numpy(g).to(dev)
+            x = torch.empty(f.shape, dtype=torch.float64, device=dev)
+            info = sc.solve_biharmonic(ft, gt, x, prec="f64", solver=solver, rtol=1e-10)
+            xh = x.cpu().numpy()
+            dur.append(time.perf_counter() - t0)
+            err_plain.append(float(np.max(np.abs(xh - ue))))
+            del ft, gt, x
         assert info["status"] == 0 and info["rel_res"] <= 1e-10, (q, info)
-        err_plain.append(float(np.max(np.abs(xh - ue))))
         iters_plain.append(info["iters"])
-        del ft, gt, x, xh
+        del xh
     cap = len(dur) / sum(dur)
     rate = args.load * cap
     arr = np.array([q["t"] for q in tr]) / rate  # trace drawn at rate 1
@@ -547,6 +571,15 @@ def run_serving(args, local):
             f, g, ue = make(q)
             ready.put((i, f, g, ue, np.empty(f.shape)))
 
+    def submit(i, f, g, x):
+        q = tr[i]
+        if q["kind"] == "ch":
+            return srv.submit_ch(f, x, (1, q["n"]), CH_DT, kappa=ch_kappa(q), prec="auto", rtol=1e-10)
+        return srv.submit(f, g, x, prec="auto", rtol=1e-10, maxit=2_000_000)
+
+    def measure(i, x, ue):
+        return float(np.linalg.norm(x)) if tr[i]["kind"] == "ch" else float(np.max(np.abs(x - ue)))
+
     prod = th.Thread(target=producer, daemon=True)
     prod.start()
     inflight, results, err_srv = {}, {}, {}
@@ -556,14 +589,14 @@ def run_serving(args, local):
         now = time.perf_counter() - t_start
         while submitted < len(tr) and arr[submitted] - arr[0] <= now:
             i, f, g, ue, x = ready.get()
-            inflight[i] = (srv.submit(f, g, x, prec="auto", rtol=1e-10, maxit=2_000_000), f, g, ue, x)
+            inflight[i] = (submit(i, f, g, x), f, g, ue, x)
             submitted += 1
         for i in list(inflight):
             t, f, g, ue, x = inflight[i]
             r = srv.poll(t)
             if r is not None:
                 results[i] = r
-                err_srv[i] = float(np.max(np.abs(x - ue)))
+                err_srv[i] = measure(i, x, ue)
                 del inflight[i]
         time.sleep(0.0002)
     served_makespan = time.perf_counter() - t_start
@@ -578,7 +611,7 @@ def run_serving(args, local):
         done_ok = 0
         for _ in range(len(tr)):
             i, f, g, ue, x = ready.get()
-            pend[i] = (srv.submit(f, g, x, prec="auto", rtol=1e-10, maxit=2_000_000), f, g, x)
+            pend[i] = (submit(i, f, g, x), f, g, x)
             for j in list(pend):
                 r = srv.poll(pend[j][0])
                 if r is not None:
@@ -598,10 +631,11 @@ def run_serving(args, local):
     lat_srv = [results[k]["latency_s"] for k in range(len(tr))]
     ok = all(results[k]["status"] == 0 and results[k]["rel_res"] <= 1e-10 for k in range(len(tr)))
     # the two paths solve the same discrete problems to the same residual: their
-    # errors against the exact solution agree to the solver tolerance's effect
+    # errors against the exact solution (plates) and their solutions' norms
+    # (Cahn-Hilliard steps) agree to the solver tolerance's effect
     dis = max(abs(err_srv[k] - err_plain[k]) / max(err_plain[k], 1e-300) for k in range(len(tr)))
     pct = lambda v, q_: float(np.percentile(np.array(v), q_))
-    n_pcg = sum(1 for q in tr if (q["n"] ** q["ndim"]) >= pcg_min)
+    n_pcg = sum(1 for q in tr if q["kind"] == "plate" and (q["n"] ** q["ndim"]) >= pcg_min)
     return {"nreq": len(tr), "rate": rate, "plain_capacity": cap, "all_converged": ok,
             "plain": {"solves_per_s": len(tr) / plain_makespan, "p50_ms": pct(lat_plain, 50) * 1e3,
                       "p99_ms": pct(lat_plain, 99) * 1e3, "capacity_solves_per_s": cap},
@@ -611,8 +645,9 @@ def run_serving(args, local):
                        "capacity_solves_per_s": burst["capacity_solves_per_s"] if burst else None,
                        "burst_all_converged": burst["all_converged"] if burst else None},
             "preconditioned_requests": n_pcg, "pcg_min_points": pcg_min,
+            "cahn_hilliard_requests": sum(1 for q in tr if q["kind"] == "ch"),
             "max_rel_diff_linf_error_served_vs_plain": dis,
-            "linf_error_vs_exact_max": max(err_plain),
+            "linf_error_vs_exact_max": max([e for q, e in zip(tr, err_plain) if q["kind"] == "plate"] or [0.0]),
             "server_end_state": st, "sizes": {"2d": [lo2, hi2], "3d": [lo3, hi3]}}
 
 
