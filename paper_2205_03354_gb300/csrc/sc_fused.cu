@@ -124,36 +124,94 @@ __device__ __forceinline__ void static_for(F &&f) {
   }
 }
 
-// One STAR factor on a run of 4 values of one row of plane k, VY rows per
-// block.  Q: the block's queue (slot C holds plane k, slots C -+ d planes
-// k -+ d); row: the run in the ring (row pitch P), whose left / right
-// neighbours and the rows above / below are read from there.  Every index is
-// a compile-time constant, so nothing is copied.
-template <int R, int NQ, int VY, int C, int VYI, int P>
-__device__ __forceinline__ void star_row(const StarW<R> W, const float (&Q)[NQ][VY][4], const float *row,
-                                         float (&out)[4]) {
-  const float4 lf = ld4s(row - 4), rt = ld4s(row + 4);
-  // rows VYI -+ d inside the block come from the queue, the others from the ring
-  float4 up[R], dn[R];
+// Packed FP32 pairs (sm_103a add/fma.rn.f32x2: two lanes per issue slot,
+// each rounded as the scalar instruction would be).
+typedef unsigned long long fpair;
+__device__ __forceinline__ fpair fp_pk(float a, float b) {
+  fpair d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ void fp_upk(fpair d, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(d));
+}
+__device__ __forceinline__ fpair fp_add(fpair a, fpair b) {
+  fpair d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ fpair fp_mul(fpair a, fpair b) {
+  fpair d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ fpair fp_fma(fpair a, fpair b, fpair c) {
+  fpair d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// One STAR factor on a block of VY rows x 4 columns of plane k.  Q: the
+// block's queue (slot C holds plane k, slots C -+ d planes k -+ d); row0:
+// the block's first row in the ring (row pitch P).  The R rows above and
+// below the block are read from the ring once, and each row's R left / right
+// neighbours with one 4- or 8-byte load per side; everything else comes from
+// the queue.  Every index is a compile-time constant, so nothing is copied.
+// Arithmetic in packed FP32 pairs, points (0, 1) and (2, 3) of a row.
+template <int R, int NQ, int VY, int C, int P>
+__device__ __forceinline__ void star_block(const StarW<R> W, const float (&Q)[NQ][VY][4], const float *row0,
+                                           float (&out)[VY][4]) {
+  static_assert(R == 1 || R == 2, "radius 1 or 2");
+  float4 up[R], dn[R];  // up[d - 1]: row -d; dn[d - 1]: row VY - 1 + d
 #pragma unroll
   for (int d = 1; d <= R; ++d) {
-    if (VYI - d < 0) up[d - 1] = ld4s(row - d * P);
-    if (VYI + d >= VY) dn[d - 1] = ld4s(row + d * P);
+    up[d - 1] = ld4s(row0 - d * P);
+    dn[d - 1] = ld4s(row0 + (VY - 1 + d) * P);
   }
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    float s = W.c * Q[C][VYI][v];
-#pragma unroll
-    for (int d = 1; d <= R; ++d) {
-      const float xm = v - d >= 0 ? Q[C][VYI][(v - d) & 3] : f4at(lf, (v - d + 4) & 3);
-      const float xp = v + d < 4 ? Q[C][VYI][(v + d) & 3] : f4at(rt, (v + d - 4) & 3);
-      const float ym = VYI - d >= 0 ? Q[C][(VYI - d) & (VY - 1)][v] : f4at(up[d - 1], v);
-      const float yp = VYI + d < VY ? Q[C][(VYI + d) & (VY - 1)][v] : f4at(dn[d - 1], v);
-      const float zs = Q[(C - d + NQ) % NQ][VYI][v] + Q[(C + d) % NQ][VYI][v];
-      s = fmaf(W.w[d - 1], (xm + xp) + (ym + yp) + zs, s);
+  const fpair wc = fp_pk(W.c, W.c);
+  static_for<0, VY>([&](auto vc) {
+    constexpr int VYI = decltype(vc)::value;
+    const float *row = row0 + VYI * P;
+    // the row with R neighbours each side: ext[R + i] is column i
+    float ext[4 + 2 * R];
+    if constexpr (R == 1) {
+      ext[0] = row[-1];
+      ext[5] = row[4];
+    } else {
+      const float2 a = *reinterpret_cast<const float2 *>(row - 2);
+      const float2 b = *reinterpret_cast<const float2 *>(row + 4);
+      ext[0] = a.x;
+      ext[1] = a.y;
+      ext[6] = b.x;
+      ext[7] = b.y;
     }
-    out[v] = s;
-  }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ext[R + i] = Q[C][VYI][i];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int v = 2 * j;
+      fpair s = fp_mul(wc, fp_pk(ext[R + v], ext[R + v + 1]));
+#pragma unroll
+      for (int d = 1; d <= R; ++d) {
+        const fpair xm = fp_pk(ext[R + v - d], ext[R + v + 1 - d]);
+        const fpair xp = fp_pk(ext[R + v + d], ext[R + v + 1 + d]);
+        fpair ym, yp;
+        if (VYI - d >= 0)
+          ym = fp_pk(Q[C][(VYI - d) & (VY - 1)][v], Q[C][(VYI - d) & (VY - 1)][v + 1]);
+        else
+          ym = fp_pk(f4at(up[(d - VYI - 1) & (R - 1)], v), f4at(up[(d - VYI - 1) & (R - 1)], v + 1));
+        if (VYI + d < VY)
+          yp = fp_pk(Q[C][(VYI + d) & (VY - 1)][v], Q[C][(VYI + d) & (VY - 1)][v + 1]);
+        else
+          yp = fp_pk(f4at(dn[(VYI + d - VY) & (R - 1)], v), f4at(dn[(VYI + d - VY) & (R - 1)], v + 1));
+        const fpair zm = fp_pk(Q[(C - d + NQ) % NQ][VYI][v], Q[(C - d + NQ) % NQ][VYI][v + 1]);
+        const fpair zp = fp_pk(Q[(C + d) % NQ][VYI][v], Q[(C + d) % NQ][VYI][v + 1]);
+        const fpair sum = fp_add(fp_add(fp_add(xm, xp), fp_add(ym, yp)), fp_add(zm, zp));
+        s = fp_fma(fp_pk(W.w[d - 1], W.w[d - 1]), sum, s);
+      }
+      fp_upk(s, out[VYI][v], out[VYI][v + 1]);
+    }
+  });
 }
 
 // t warps (the first NTW): thread i < NTB owns t block (i % NBX, i / NBX)
@@ -262,15 +320,11 @@ __global__ void __launch_bounds__(Fused3<R>::NTHR, 2)
         const float *xc = xr + ((u - R + K::NQ) % K::NXS) * K::XPL;
         float *tw = tr + ((u - R + K::NQ) % K::NTS) * K::TPL + trow * K::TC + tcol;
         constexpr int CS = (u - R + K::NQ) % K::NQ;
+        float out[K::VY][4];
+        star_block<R, K::NQ, K::VY, CS, K::XC>(WA, q, xc + xrow * K::XC + xcol, out);
 #pragma unroll
-        for (int vy = 0; vy < K::VY; ++vy) {
-          float out[4];
-          if (vy == 0)
-            star_row<R, K::NQ, K::VY, CS, 0, K::XC>(WA, q, xc + xrow * K::XC + xcol, out);
-          else
-            star_row<R, K::NQ, K::VY, CS, 1, K::XC>(WA, q, xc + (xrow + 1) * K::XC + xcol, out);
-          *reinterpret_cast<float4 *>(tw + vy * K::TC) = make_float4(out[0], out[1], out[2], out[3]);
-        }
+        for (int vy = 0; vy < K::VY; ++vy)
+          *reinterpret_cast<float4 *>(tw + vy * K::TC) = make_float4(out[vy][0], out[vy][1], out[vy][2], out[vy][3]);
       } else {
         // ---- t(q'), q' = p_{s-1} - R, into the queue; y(q' - R) once 2R t planes are queued ----
         const int s1 = s - 1;
@@ -290,13 +344,11 @@ __global__ void __launch_bounds__(Fused3<R>::NTHR, 2)
         const float *tc = tr + ((u1 - 2 * R + 2 * K::NQ) % K::NTS) * K::TPL + trow * K::TC + tcol;
         constexpr int CS = (u + K::NQ - 1 - R + K::NQ) % K::NQ;
         const int xo = x0 - K::HXT + tcol;
+        float outb[K::VY][4];
+        star_block<R, K::NQ, K::VY, CS, K::TC>(WB, q, tc, outb);
 #pragma unroll
         for (int vy = 0; vy < K::VY; ++vy) {
-          float out[4];
-          if (vy == 0)
-            star_row<R, K::NQ, K::VY, CS, 0, K::TC>(WB, q, tc, out);
-          else
-            star_row<R, K::NQ, K::VY, CS, 1, K::TC>(WB, q, tc + K::TC, out);
+          const float(&out)[4] = outb[vy];
           const int yy = y0 - K::HYT + trow + vy;
           if (yy < g.ny && j < zend) {
             float *dst = y + (long long)j * g.out_ss + (long long)yy * g.out_sy + xo;
