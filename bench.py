@@ -298,9 +298,10 @@ def run_apply_one(args, local):
 def run_apply_e2e(sc, cases, dev, stream, args, world):
     """The sweep through the host-buffer entry point: every step copies each
     case's x from pinned host memory, applies the tuned schedule and copies y
-    back (sc_apply_tuned_host, asynchronous: the next case's copy-in overlaps
-    the previous case's copy-out); the host waits for the stream at the end
-    of each step.  Every step is timed."""
+    back (sc_apply_tuned_host: slabs along the slowest axis, with one slab's
+    copy-in, the previous slab's apply and the one before's copy-out in
+    flight at once); the host waits for the stream at the end of each step.
+    Every step is timed."""
     import torch
     hosts = []
     maxb = 0
@@ -324,15 +325,22 @@ def run_apply_e2e(sc, cases, dev, stream, args, world):
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    per_step = []
     for _ in range(nsteps):
+        ts = time.perf_counter()
         step()
+        per_step.append(time.perf_counter() - ts)
     t1 = time.perf_counter()
     barrier(world)
     # the last step's results against the device-only path (same schedule: same bits)
     ok = all(torch.equal(yh.reshape(-1)[::997], c["y"].reshape(-1)[::997].cpu())
              for (xh, yh), c in zip(hosts, cases))
     sec = (t1 - t0) / nsteps
-    h2d = sum(c["bytes"] // 2 for c in cases)
+    # bytes read from host memory per step: each case's x once, plus the
+    # 2 Rc planes (Rc = 4) the periodic halo wraps in at the first and last
+    # slab (the halo planes consecutive slabs share move device to device)
+    h2d = sum(c["bytes"] // 2 * (c["n"] + 8) // c["n"] for c in cases)
+    d2h = sum(c["bytes"] // 2 for c in cases)
     # the link alone: the same bytes copied in, out, and both at once
     s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     scratch = [(c["x"], c["y"]) for c in cases]
@@ -352,9 +360,13 @@ def run_apply_e2e(sc, cases, dev, stream, args, world):
 
     for d in ("in", "out", "both"):  # first use of the copy streams
         copies(d)
-    link = {"h2d_gbs": h2d / copies("in") / 1e9, "d2h_gbs": h2d / copies("out") / 1e9,
-            "both_gbs": 2 * h2d / copies("both") / 1e9}
-    return {"sec_per_step": sec, "gbs": sum(c["bytes"] for c in cases) / sec / 1e9, "h2d": h2d, "d2h": h2d,
+    xb = d2h
+    link = {"h2d_gbs": xb / copies("in") / 1e9, "d2h_gbs": xb / copies("out") / 1e9,
+            "both_gbs": 2 * xb / copies("both") / 1e9}
+    per_step.sort()
+    return {"sec_per_step": sec, "gbs": sum(c["bytes"] for c in cases) / sec / 1e9, "h2d": h2d, "d2h": d2h,
+            "step_ms": {"median": round(per_step[len(per_step) // 2] * 1e3, 2), "min": round(per_step[0] * 1e3, 2),
+                        "max": round(per_step[-1] * 1e3, 2)},
             "steps": nsteps, "matches_device_path": bool(ok), "link": link}
 
 
@@ -951,8 +963,9 @@ def main():
         e_sec = max_over_ranks(res["e2e"]["sec_per_step"], world)
         e2e = {"value": world * res["step_bytes"] / e_sec / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": world * res["e2e"]["h2d"], "d2h_bytes_per_step": world * res["e2e"]["d2h"],
-               "path": "sc_apply_tuned_host (pinned host x/y; copy-in of the next case overlaps copy-out)",
-               "steps_timed": res["e2e"]["steps"], "matches_device_path": res["e2e"]["matches_device_path"],
+               "path": "sc_apply_tuned_host (pinned host x/y; ~8 z-slabs per case, copy-in / apply / copy-out of consecutive slabs overlapped on three streams)",
+               "steps_timed": res["e2e"]["steps"], "step_ms": res["e2e"]["step_ms"],
+               "matches_device_path": res["e2e"]["matches_device_path"],
                "link_alone": {k: round(v, 1) for k, v in res["e2e"]["link"].items()}}
     serving = None
     if rank == 0 and not args.no_serving:

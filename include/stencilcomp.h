@@ -235,16 +235,28 @@ int sc_apply_tuned(const sc_stencil *outer, const sc_stencil *inner, int32_t dty
 int sc_tuned_choice(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,
                     const int64_t *dims, sc_tune_choice *out);
 /* The tuned apply (as sc_apply_tuned) with x and y in HOST memory, for data
- * that lives on the host: x is copied into the device work space on a
- * library copy-in stream, the tuned schedule runs on `stream`, y is copied
- * back on a library copy-out stream, and `stream` is made to wait for that
- * copy.  Asynchronous: synchronise `stream` before reading y_host.  Pinned
- * host buffers let the copies run at link speed.  Consecutive calls on one
- * device overlap: the next call's copy-in (which waits only until the
- * previous apply has read its input) runs while the previous result is
- * copied out.  work_bytes >= sc_apply_tuned_host_work_bytes(...); one work
- * space may serve consecutive calls.  Calls from several host threads are
- * serialised by the library. */
+ * that lives on the host.  The grid is cut along its slowest axis (z in 3D,
+ * y in 2D) into about eight slabs of at least 4 (R_outer + R_inner) planes;
+ * for each slab the input planes it reads (its planes and that halo) are
+ * copied into the device work space on a library copy-in stream (the halo
+ * planes shared with the previous slab device to device), the in-plane
+ * boundary ring is filled on the device, the tuned schedule of the WHOLE
+ * grid's shape runs on the slab (as a ghosted grid) on `stream`, and the
+ * slab's output planes are copied back on a library copy-out stream; two
+ * buffer sets alternate, so slab k + 1's copy-in, slab k's apply and slab
+ * k - 1's copy-out overlap.  Grids shorter than two slabs are copied, applied
+ * and copied back whole.  The result equals sc_apply_tuned's on the same
+ * grid bit for bit, except for a pair-arithmetic schedule with radius-1
+ * factors on a periodic grid, whose slabs run the native FP64 nested passes
+ * (within the FP64 apply tolerance).  Asynchronous: `stream` is made to wait
+ * for the last copy-out; synchronise it before reading y_host.  Consecutive
+ * calls on one device overlap (a call's first copy-in waits only until the
+ * previous call's applies have read their inputs).  x_host and y_host must
+ * not overlap (SC_EINVAL); pinned host buffers let the copies run at link
+ * speed.  work_bytes >= sc_apply_tuned_host_work_bytes(...) (about two slabs
+ * of input and output plus the schedule's work space for one slab; the
+ * whole-grid size for short grids); one work space may serve consecutive
+ * calls.  Calls from several host threads are serialised by the library. */
 size_t sc_apply_tuned_host_work_bytes(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype,
                                       int32_t bc, const int64_t *dims);
 int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_t dtype, int32_t bc,

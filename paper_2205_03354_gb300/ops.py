@@ -208,7 +208,10 @@ def apply_tuned_host_work_bytes(outer: Stencil, inner: Stencil, dtype, bc, dims)
 
 def apply_tuned_host(outer: Stencil, inner: Stencil, x, y, work, bc="periodic", h=(1, 1), dims=None, stream=None):
     """The tuned apply with x and y in host memory (pinned for link-speed
-    copies).  Asynchronous: synchronise the stream before reading y."""
+    copies), pipelined over slabs of the slowest axis: one slab's copy-in,
+    the previous slab's apply and the one before's copy-out run at once.
+    x and y must not overlap.  Asynchronous: synchronise the stream before
+    reading y."""
     for name, t in (("x", x), ("y", y)):
         if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.is_contiguous()):
             raise ValueError(f"{name} must be a contiguous host tensor")

@@ -103,15 +103,17 @@ def test_other_supports(dt):
             check(yt.cpu().numpy(), x, w, bc, os_.radius, dt, os_.npts)
 
 
-@pytest.mark.parametrize("ndim,dims,dt,bc", [(2, (520, 257), np.float64, "periodic"),
-                                          (3, (96, 80, 72), np.float32, "periodic"),
-                                          (3, (40, 30, 20), np.float64, "ghosted"),
+@pytest.mark.parametrize("ndim,dims,dt,bc", [(2, (520, 257), np.float64, "periodic"),   # 8 slabs, ragged
+                                          (3, (96, 80, 72), np.float32, "periodic"),   # 5 slabs
+                                          (3, (40, 30, 20), np.float64, "ghosted"),    # whole grid
+                                          (3, (48, 40, 70), np.float64, "ghosted"),    # 5 slabs
+                                          (3, (36, 28, 66), np.float32, "zero"),
                                           (2, (300, 77), np.float32, "zero")])
 def test_tuned_host_entry_point_matches_device_one(ndim, dims, dt, bc):
-    """The asynchronous host-buffer tuned apply, called three times in a row
-    on one work space with different inputs (copy-in of a call overlapping
-    the previous copy-out): each result equals the device-buffer tuned apply
-    bit for bit."""
+    """The asynchronous host-buffer tuned apply (slab pipeline, or the whole
+    grid when it is shorter than two slabs), called three times in a row on
+    one work space with different inputs: each result equals the
+    device-buffer tuned apply bit for bit."""
     L = sc.laplacian(ndim, 4)
     R = 4
     shape = tuple(reversed(dims))
@@ -129,6 +131,91 @@ def test_tuned_host_entry_point_matches_device_one(ndim, dims, dt, bc):
         sc.apply_tuned(L, L, x.to(DEV), yd, wd, bc=bc, h=(1, dims[0]), dims=dims)
         torch.cuda.synchronize()
         assert torch.equal(yd.cpu(), y)
+
+
+def _host_vs_device(L, ndim, dims, dt, bc, seed):
+    R = 2 * L.radius
+    shape = tuple(reversed(dims))
+    xshape = tuple(v + 2 * R for v in shape) if bc == "ghosted" else shape
+    x = torch.from_numpy(fields.uniform(xshape, seed=seed, dtype=dt)).pin_memory()
+    y = torch.full(shape, float("nan"), dtype=x.dtype).pin_memory()
+    work = torch.empty(sc.apply_tuned_host_work_bytes(L, L, x.dtype, bc, dims), dtype=torch.uint8, device=DEV)
+    sc.apply_tuned_host(L, L, x, y, work, bc=bc, h=(1, dims[0]), dims=dims)
+    torch.cuda.current_stream().synchronize()
+    wd = torch.empty(sc.apply_composition_work_bytes(L, L, x.dtype, bc, dims), dtype=torch.uint8, device=DEV)
+    yd = torch.empty(shape, dtype=x.dtype, device=DEV)
+    sc.apply_tuned(L, L, x.to(DEV), yd, wd, bc=bc, h=(1, dims[0]), dims=dims)
+    torch.cuda.synchronize()
+    return y, yd.cpu()
+
+
+@pytest.mark.parametrize("ndim,dims,dt,bc,how,planes", [
+    (3, (80, 48, 64), np.float32, "periodic", "fused", 0),
+    (2, (256, 200), np.float32, "periodic", "fused", 64),
+    (3, (72, 40, 66), np.float32, "zero", "nested", 16),
+    (3, (64, 40, 48), np.float64, "periodic", "pair", 0),
+    (2, (512, 300), np.float64, "periodic", "pair", 32),
+    (3, (48, 36, 40), np.float64, "zero", "pair", 0),
+    (3, (40, 36, 50), np.float64, "ghosted", "pair", 16),
+])
+def test_host_slabs_run_the_whole_grid_schedule(ndim, dims, dt, bc, how, planes):
+    """Each slab of the host-buffer pipeline runs the schedule recorded for
+    the whole grid (fused, nested or pair arithmetic, with its planes per
+    CTA) on a ghosted slab: the result equals the device apply of the whole
+    grid bit for bit."""
+    L = sc.laplacian(ndim, 4)
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    sc.tune_set(L, L, tdt, bc, dims, {"eval": how, "planes": planes})
+    y, yd = _host_vs_device(L, ndim, dims, dt, bc, seed=61)
+    assert torch.equal(y, yd)
+
+
+def test_host_slabs_radius_one_pair_runs_native():
+    """Pair arithmetic with radius-1 factors has no ghosted form: the slabs of
+    a periodic grid run the native FP64 nested passes, within the FP64 apply
+    tolerance of the whole-grid pair apply."""
+    L = sc.laplacian(3, 2)
+    dims = (64, 40, 48)
+    sc.tune_set(L, L, torch.float64, "periodic", dims, {"eval": "pair", "planes": 0})
+    y, yd = _host_vs_device(L, 3, dims, np.float64, "periodic", seed=62)
+    err = (y - yd).abs().max().item()
+    assert err <= 1e-11 * yd.abs().max().item()
+
+
+def test_host_pipeline_alternating_shapes_on_one_work_space():
+    """Calls of different shapes back to back on one work space (the second
+    call's staging lies where the first call's output buffers were): every
+    result equals its device apply bit for bit."""
+    L = sc.laplacian(3, 4)
+    shapes = [(96, 64, 80), (40, 24, 36), (96, 64, 80), (64, 48, 20)]
+    wb = max(sc.apply_tuned_host_work_bytes(L, L, torch.float64, "periodic", d) for d in shapes)
+    work = torch.empty(wb, dtype=torch.uint8, device=DEV)
+    xs, ys = [], []
+    for k, d in enumerate(shapes):
+        x = torch.from_numpy(fields.uniform(tuple(reversed(d)), seed=70 + k, dtype=np.float64)).pin_memory()
+        y = torch.full(tuple(reversed(d)), float("nan"), dtype=torch.float64).pin_memory()
+        sc.apply_tuned_host(L, L, x, y, work, bc="periodic", h=(1, d[0]), dims=d)
+        xs.append(x)
+        ys.append(y)
+    torch.cuda.current_stream().synchronize()
+    for d, x, y in zip(shapes, xs, ys):
+        wd = torch.empty(sc.apply_composition_work_bytes(L, L, torch.float64, "periodic", d), dtype=torch.uint8,
+                         device=DEV)
+        yd = torch.empty(tuple(reversed(d)), dtype=torch.float64, device=DEV)
+        sc.apply_tuned(L, L, x.to(DEV), yd, wd, bc="periodic", h=(1, d[0]), dims=d)
+        torch.cuda.synchronize()
+        assert torch.equal(yd.cpu(), y)
+
+
+def test_host_pipeline_refuses_overlapping_host_buffers():
+    L = sc.laplacian(2, 4)
+    dims = (256, 128)
+    x = torch.zeros(2 * 256 * 128, dtype=torch.float64).pin_memory()
+    work = torch.empty(sc.apply_tuned_host_work_bytes(L, L, torch.float64, "periodic", dims), dtype=torch.uint8,
+                       device=DEV)
+    with pytest.raises(sc.ScError):
+        sc.apply_tuned_host(L, L, x[:256 * 128], x[100:100 + 256 * 128], work, bc="periodic", h=(1, 256),
+                            dims=dims)
 
 
 def test_host_buffer_entry_point_matches_device_one():

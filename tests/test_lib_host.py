@@ -5,6 +5,7 @@ import math
 from fractions import Fraction
 
 import numpy as np
+import torch
 import pytest
 
 from tests.libutil import ensure_built, header_functions
@@ -224,3 +225,21 @@ def test_composition_overflow_is_refused():
     with pytest.raises(sc.ScError) as e:
         sc.compose_stencil(big, big)  # 2^80
     assert e.value.status == 8
+
+
+def test_host_pipeline_work_space_is_two_slabs():
+    """The host-buffer apply stages about two slabs (an eighth of the grid
+    each, plus the composed halo) instead of the whole grid once the slowest
+    axis holds two slabs of 4 Rc planes; shorter grids take the whole-grid
+    space (input with its ring, output, schedule work)."""
+    L = sc.laplacian(3, 4)
+    es = 8
+    big = (512, 512, 512)
+    whole = 2 * 512 ** 3 * es
+    wb = sc.apply_tuned_host_work_bytes(L, L, torch.float64, "periodic", big)
+    assert 0 < wb < 0.9 * whole
+    # two staging + two ring-filled + two output slabs of 64 planes (+ 8 halo)
+    assert wb >= (2 * 72 * 512 * 512 + 2 * 72 * 520 * 520 + 2 * 64 * 512 * 512) * es
+    short = (64, 64, 31)  # 31 < 2 x 16 planes: whole grid
+    wb = sc.apply_tuned_host_work_bytes(L, L, torch.float64, "ghosted", short)
+    assert wb >= (72 * 72 * 39 + 64 * 64 * 31) * es
