@@ -12,16 +12,19 @@
 // iterations (measured 10-31 from N = 32 to 512 in 2D).
 //
 // The preconditioner runs in FP32: each axis transform is a dense product
-// with S (an FP32 GEMM kernel of this file, batched over the other axes),
-// then the diagonal scaling, then the transforms again.  Everything else --
+// with S (a cuBLAS GEMM, batched over the other axes, with FP32 accuracy
+// emulated on the BF16 tensor cores), then the diagonal scaling, then the
+// transforms again; the lowest K0^d modes are transformed in FP64.  Everything else --
 // x, r, p, the products A p, the dot products -- stays in FP64, and because
 // an FP32 preconditioner is not exactly the same linear map at every use, the
 // update of the search direction uses the flexible (Polak-Ribiere) form
 // beta = z_new . (r_new - r_old) / (z_old . r_old), with r_new - r_old =
 // -alpha A p.  Convergence is declared on the FP64 true residual.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -36,10 +39,9 @@
 namespace sc {
 
 // ---------------------------------------------------------------------------
-// FP32 GEMM, row-major, strided batches: C[b] = A[b] (M x K) * B[b] (K x N)
+// Dense products of the transforms (cuBLAS), row-major, strided batches:
+// C[b] = A[b] (M x K) * B[b] (K x N)
 // ---------------------------------------------------------------------------
-
-constexpr int GM_BM = 64, GM_BN = 64, GM_BK = 16, GM_NTHR = 256;
 
 template <typename T>
 struct GemmArgs {
@@ -48,180 +50,57 @@ struct GemmArgs {
   int M, N, K;
   long long lda, ldb, ldc;
   long long sa, sb, sc;  // batch strides (0: shared operand)
-  int ksplit = 1;        // > 1: K in ksplit slices, slice s of batch b written
-  T *part = nullptr;     // densely to part[(s * batch + b) * M * N], then summed
-  int batch = 1;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(GM_NTHR) k_gemm(GemmArgs<T> g) {
-  __shared__ T As[GM_BK][GM_BM + 4];  // transposed: As[k][m]
-  __shared__ T Bs[GM_BK][GM_BN + 4];
-  const int b = blockIdx.z / g.ksplit, ks = blockIdx.z % g.ksplit;
-  const T *A = g.A + b * g.sa, *B = g.B + b * g.sb;
-  T *C = g.C + b * g.sc;
-  long long ldc = g.ldc;
-  if (g.ksplit > 1) {
-    C = g.part + ((long long)ks * g.batch + b) * g.M * g.N;
-    ldc = g.N;
+// One cuBLAS handle per host thread and device (the server's scheduler
+// threads and callers' threads never share one), destroyed at thread exit.
+struct BlasHandles {
+  cublasHandle_t h[64] = {};
+  ~BlasHandles() {
+    for (cublasHandle_t &x : h)
+      if (x) cublasDestroy(x);
   }
-  // this slice's K range, in whole tiles
-  const int kt = (g.K + GM_BK - 1) / GM_BK, kper = (kt + g.ksplit - 1) / g.ksplit;
-  const int kbeg = ks * kper * GM_BK, kend = min(g.K, (ks + 1) * kper * GM_BK);
-  const int m0 = blockIdx.y * GM_BM, n0 = blockIdx.x * GM_BN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 outputs each
-  T acc[4][4] = {};
-  for (int k0 = kbeg; k0 < kend; k0 += GM_BK) {
-    // A tile: 64 x 16 (4 per thread); B tile: 16 x 64 (4 per thread)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = threadIdx.x + i * GM_NTHR;
-      const int am = e / GM_BK, ak = e % GM_BK;
-      const int gm = m0 + am, gk = k0 + ak;
-      As[ak][am] = (gm < g.M && gk < kend) ? A[(long long)gm * g.lda + gk] : T(0);
-      const int bk = e / GM_BN, bn = e % GM_BN;
-      const int hk = k0 + bk, hn = n0 + bn;
-      Bs[bk][bn] = (hk < kend && hn < g.N) ? B[(long long)hk * g.ldb + hn] : T(0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < GM_BK; ++k) {
-      T a[4], bb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty * 4 + i;
-    if (gm >= g.M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx * 4 + j;
-      if (gn < g.N) C[(long long)gm * ldc + gn] = acc[i][j];
-    }
-  }
+};
+
+static cublasHandle_t blas_handle() {
+  thread_local BlasHandles hs;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cublasHandle_t &h = hs.h[dev & 63];
+  if (!h && cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) h = nullptr;
+  return h;
 }
 
-// FP32 GEMM for the large transforms: 128 x 128 output tiles, K in steps of
-// 8, 256 threads with 8 x 8 outputs each (two 4 x 4 quadrants, so that the
-// shared-memory reads are broadcasts / consecutive 16-byte words); the next
-// K step is loaded into registers while the current one is multiplied (two
-// shared buffers, one barrier per step).  Edges are predicated.
-constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8, SG_PAD = 4;
-
-__global__ void __launch_bounds__(256) k_sgemm128(GemmArgs<float> g) {
-  __shared__ __align__(16) float As[2][SG_BK][SG_BM + SG_PAD];
-  __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
-  const int b = blockIdx.z;
-  const float *A = g.A + b * g.sa, *B = g.B + b * g.sb;
-  float *C = g.C + b * g.sc;
-  const int m0 = blockIdx.y * SG_BM, n0 = blockIdx.x * SG_BN;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  float ra[4], rb[4];
-  auto fetch = [&](int k0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + i * 256;
-      const int am = e / SG_BK, ak = e % SG_BK, gm = m0 + am, gk = k0 + ak;
-      ra[i] = (gm < g.M && gk < g.K) ? __ldg(A + (long long)gm * g.lda + gk) : 0.0f;
-      const int bk = e / SG_BN, bn = e % SG_BN, hk = k0 + bk, hn = n0 + bn;
-      rb[i] = (hk < g.K && hn < g.N) ? __ldg(B + (long long)hk * g.ldb + hn) : 0.0f;
-    }
-  };
-  auto stash = [&](int buf) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + i * 256;
-      As[buf][e % SG_BK][e / SG_BK] = ra[i];
-      Bs[buf][e / SG_BN][e % SG_BN] = rb[i];
-    }
-  };
-  float acc[8][8] = {};
-  fetch(0);
-  stash(0);
-  __syncthreads();
-  int buf = 0;
-  for (int k0 = 0; k0 < g.K; k0 += SG_BK) {
-    const bool more = k0 + SG_BK < g.K;
-    if (more) fetch(k0 + SG_BK);
-#pragma unroll
-    for (int k = 0; k < SG_BK; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
-      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
-      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    if (more) {
-      stash(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
-    if (gm >= g.M) continue;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-      if (gn < g.N) C[(long long)gm * g.ldc + gn] = acc[i][j];
-    }
-  }
-}
-
-// C[b] = sum over slices s of part[s][b] (fixed order: deterministic).
+// The FP32 transforms run with FP32 accuracy emulated on the BF16 tensor
+// cores (each operand split into three BF16 parts, nine products, FP32
+// accumulation; cuBLAS picks the emulation where it is faster and the native
+// pipe otherwise; a library without that compute type runs the native one).
+// The FP64 low-mode products stay native FP64: the fixed-point emulation left
+// an algebraic error of 1e-8 in the 2048^2 plate solution at a residual of
+// 1e-10 (native: below 1e-9).
 template <typename T>
-__global__ void k_gemm_reduce(GemmArgs<T> g) {
-  const long long mn = (long long)g.M * g.N, n = mn * g.batch;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long b = i / mn, e = i % mn, m = e / g.N, c = e % g.N;
-    T s = T(0);
-    for (int k = 0; k < g.ksplit; ++k) s += g.part[(long long)k * n + i];
-    g.C[b * g.sc + m * g.ldc + c] = s;
+static int gemm(const GemmArgs<T> &g, int batch, cudaStream_t st) {
+  static std::atomic<int> emulate{1};
+  cublasHandle_t h = blas_handle();
+  if (!h) return fail(SC_ECUDA, "cuBLAS handle creation failed");
+  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(SC_ECUDA, "cuBLAS stream");
+  const cudaDataType_t dt = sizeof(T) == 8 ? CUDA_R_64F : CUDA_R_32F;
+  const T one = T(1), zero = T(0);
+  // row-major C = A B is column-major C^T = B^T A^T
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool em = emulate.load(std::memory_order_relaxed) != 0;
+    if (pass == 1 && em) break;
+    cublasComputeType_t ct =
+        sizeof(T) == 8 ? CUBLAS_COMPUTE_64F : (em ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F);
+    const cublasStatus_t s = cublasGemmStridedBatchedEx(
+        h, CUBLAS_OP_N, CUBLAS_OP_N, g.N, g.M, g.K, &one, g.B, dt, int(g.ldb), g.sb, g.A, dt, int(g.lda), g.sa,
+        &zero, g.C, dt, int(g.ldc), g.sc, batch, ct, CUBLAS_GEMM_DEFAULT);
+    if (s == CUBLAS_STATUS_SUCCESS) return SC_OK;
+    if (!em || sizeof(T) == 8 || (s != CUBLAS_STATUS_NOT_SUPPORTED && s != CUBLAS_STATUS_INVALID_VALUE))
+      return fail(SC_ECUDA, "cuBLAS GEMM failed (status %d)", int(s));
+    emulate.store(0);  // retry with the native compute type
   }
-}
-
-template <typename T>
-static void gemm(GemmArgs<T> g, int batch, cudaStream_t st, T *part = nullptr, long long part_cap = 0) {
-  const long long ctas = (long long)((g.N + GM_BN - 1) / GM_BN) * ((g.M + GM_BM - 1) / GM_BM) * batch;
-  // FP64 tiles are slow per SM: split K until about two CTAs per SM
-  int ks = 1;
-  if (part && sizeof(T) == 8) {
-    const long long want = (2LL * num_sms() + ctas - 1) / ctas;
-    ks = int(std::max<long long>(1, std::min<long long>(want, g.K / (4 * GM_BK))));
-    while (ks > 1 && (long long)ks * g.M * g.N * batch > part_cap) --ks;
-  }
-  g.ksplit = ks;
-  g.part = part;
-  g.batch = batch;
-  if constexpr (sizeof(T) == 4) {
-    if (g.M >= SG_BM && g.N >= SG_BN) {
-      dim3 grid128((g.N + SG_BN - 1) / SG_BN, (g.M + SG_BM - 1) / SG_BM, batch);
-      k_sgemm128<<<grid128, 256, 0, st>>>(g);
-      return;
-    }
-  }
-  dim3 grid((g.N + GM_BN - 1) / GM_BN, (g.M + GM_BM - 1) / GM_BM, batch * ks);
-  k_gemm<T><<<grid, GM_NTHR, 0, st>>>(g);
-  if (ks > 1) {
-    const long long n = (long long)g.M * g.N * batch;
-    k_gemm_reduce<T><<<int(std::min<long long>((n + 255) / 256, 8LL * num_sms())), 256, 0, st>>>(g);
-  }
+  return fail(SC_ECUDA, "cuBLAS GEMM failed");
 }
 
 // ---------------------------------------------------------------------------
@@ -288,15 +167,20 @@ __global__ void k_to_f64(const float *__restrict__ a, double *__restrict__ b, lo
 // u /= (sum_a lam1[k_a])^2 on the N^ndim grid (k_a the index along axis a),
 // except on the low block (every k_a < K0), which is set to zero: those
 // modes are handled in FP64.
-__global__ void k_inv_lambda2(float *__restrict__ u, const double *__restrict__ lam1, int N, int ndim,
-                              long long n, int K0) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = int(i % N), ky = int((i / N) % N), kz = ndim == 3 ? int(i / ((long long)N * N)) : 0;
-    double l = lam1[kx] + lam1[ky];
-    if (ndim == 3) l += lam1[kz];
-    const bool low = kx < K0 && ky < K0 && kz < K0;
-    u[i] = low ? 0.0f : float(double(u[i]) / (l * l));
+// u /= Lambda^2 mode by mode in FP32 (the transforms around it are FP32),
+// zero on the low block that the FP64 products handle.  Blocks stride over
+// the grid rows (ky, kz), threads over kx: no 64-bit index division.
+__global__ void k_inv_lambda2(float *__restrict__ u, const double *__restrict__ lam1, int N, int ndim, int K0) {
+  const long long rows = ndim == 3 ? (long long)N * N : N;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int ky = int(row % N), kz = ndim == 3 ? int(row / N) : 0;
+    const float lyz = float(lam1[ky] + (ndim == 3 ? lam1[kz] : 0.0));
+    const bool low_yz = ky < K0 && kz < K0;
+    float *ur = u + row * N;
+    for (int kx = threadIdx.x; kx < N; kx += blockDim.x) {
+      const float l = float(lam1[kx]) + lyz;
+      ur[kx] = (low_yz && kx < K0) ? 0.0f : ur[kx] / (l * l);
+    }
   }
 }
 
@@ -389,69 +273,70 @@ static int grid_for(long long n) { return int(std::min<long long>((n + 255) / 25
 
 // u <- u transformed by S along every axis (ping-pong through w; the result
 // ends in u).  Grid layout [z][y][x], N points per axis.
-static void dst_all(float *u, float *w, const float *S, int N, int ndim, cudaStream_t st) {
+static int dst_all(float *u, float *w, const float *S, int N, int ndim, cudaStream_t st) {
   const long long N2 = (long long)N * N;
   // x axis: rows of N values times S (S symmetric): C = U S
-  {
-    GemmArgs<float> g{u, S, w, int(ndim == 3 ? N2 : N), N, N, N, N, N, 0, 0, 0};
-    gemm(g, 1, st);
-  }
-  if (ndim == 2) {  // y axis: C = S W
-    GemmArgs<float> g{S, w, u, N, N, N, N, N, N, 0, 0, 0};
-    gemm(g, 1, st);
-    return;
-  }
-  {  // y axis, one z plane per batch: C_z = S W_z
-    GemmArgs<float> g{S, w, u, N, N, N, N, N, N, 0, N2, N2};
-    gemm(g, N, st);
-  }
-  {  // z axis: C = S U viewed as N x N^2
-    GemmArgs<float> g{S, u, w, N, int(N2), N, N, N2, N2, 0, 0, 0};
-    gemm(g, 1, st);
-  }
+  if (int rc = gemm(GemmArgs<float>{u, S, w, int(ndim == 3 ? N2 : N), N, N, N, N, N, 0, 0, 0}, 1, st)) return rc;
+  if (ndim == 2)  // y axis: C = S W
+    return gemm(GemmArgs<float>{S, w, u, N, N, N, N, N, N, 0, 0, 0}, 1, st);
+  // y axis, one z plane per batch: C_z = S W_z
+  if (int rc = gemm(GemmArgs<float>{S, w, u, N, N, N, N, N, N, 0, N2, N2}, N, st)) return rc;
+  // z axis: C = S U viewed as N x N^2
+  if (int rc = gemm(GemmArgs<float>{S, u, w, N, int(N2), N, N, N2, N2, 0, 0, 0}, 1, st)) return rc;
   cudaMemcpyAsync(u, w, size_t(N2) * N * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  return SC_OK;
 }
 
-int pcg_low_modes(int ndim, long long N) { return int(std::min<long long>(N, ndim == 3 ? 16 : 64)); }
-
-// FP64 GEMM with split-K partials in the preconditioner's work space.
-static void gemmd(const ProbAux &aux, const GemmArgs<double> &g, int batch, cudaStream_t st) {
-  gemm<double>(g, batch, st, aux.gp, aux.gp_cap);
+// 16^ndim lowest modes: a 2048^2 plate converges in 85 iterations with it
+// (81 with 64^2 FP64 modes, at twice the FP64 product time per iteration).
+int pcg_low_modes(int ndim, long long N) {
+  (void)ndim;
+  return int(std::min<long long>(N, 16));
 }
 
 // zl = S_low^T Lambda^-2 S_low r over the K0^ndim lowest modes, in FP64.
-static void precond_low(const double *r, const ProbAux &aux, int N, int K0, int ndim, cudaStream_t st) {
+static int precond_low(const double *r, const ProbAux &aux, int N, int K0, int ndim, cudaStream_t st) {
   const long long N2 = (long long)N * N, K2 = (long long)K0 * K0;
+  typedef GemmArgs<double> G;
   if (ndim == 2) {
-    gemmd(aux, GemmArgs<double>{r, aux.SlT, aux.wa, N, K0, N, N, K0, K0, 0, 0, 0}, 1, st);        // (y, kx)
-    gemmd(aux, GemmArgs<double>{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, 0, 0}, 1, st);   // (ky, kx)
+    const G g1{r, aux.SlT, aux.wa, N, K0, N, N, K0, K0, 0, 0, 0};            // (y, kx)
+    const G g2{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, 0, 0};       // (ky, kx)
+    const G g3{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, 0, 0};     // (y, kx)
+    const G g4{aux.wa, aux.Sl, aux.zl, N, N, K0, K0, N, N, 0, 0, 0};         // (y, x)
+    if (int rc = gemm(g1, 1, st)) return rc;
+    if (int rc = gemm(g2, 1, st)) return rc;
     k_low_scale<<<grid_for(K2), 256, 0, st>>>(aux.wb, aux.lam1, K0, 2);
-    gemmd(aux, GemmArgs<double>{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, 0, 0}, 1, st);  // (y, kx)
-    gemmd(aux, GemmArgs<double>{aux.wa, aux.Sl, aux.zl, N, N, K0, K0, N, N, 0, 0, 0}, 1, st);      // (y, x)
-    return;
+    if (int rc = gemm(g3, 1, st)) return rc;
+    return gemm(g4, 1, st);
   }
-  gemmd(aux, GemmArgs<double>{r, aux.SlT, aux.wa, int(N2), K0, N, N, K0, K0, 0, 0, 0}, 1, st);     // (z, y, kx)
-  gemmd(aux, GemmArgs<double>{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, (long long)N * K0, K2}, N,
-       st);                                                                                  // (z, ky, kx)
-  gemmd(aux, GemmArgs<double>{aux.Sl, aux.wb, aux.wc, K0, int(K2), N, N, K2, K2, 0, 0, 0}, 1, st);  // (kz, ky, kx)
+  const G g1{r, aux.SlT, aux.wa, int(N2), K0, N, N, K0, K0, 0, 0, 0};                    // (z, y, kx)
+  const G g2{aux.Sl, aux.wa, aux.wb, K0, K0, N, N, K0, K0, 0, (long long)N * K0, K2};    // (z, ky, kx)
+  const G g3{aux.Sl, aux.wb, aux.wc, K0, int(K2), N, N, K2, K2, 0, 0, 0};                // (kz, ky, kx)
+  const G g4{aux.SlT, aux.wc, aux.wb, N, int(K2), K0, K0, K2, K2, 0, 0, 0};              // (z, ky, kx)
+  const G g5{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, K2, (long long)N * K0};  // (z, y, kx)
+  const G g6{aux.wa, aux.Sl, aux.zl, int(N2), N, K0, K0, N, N, 0, 0, 0};                 // (z, y, x)
+  if (int rc = gemm(g1, 1, st)) return rc;
+  if (int rc = gemm(g2, N, st)) return rc;
+  if (int rc = gemm(g3, 1, st)) return rc;
   k_low_scale<<<grid_for(K2 * K0), 256, 0, st>>>(aux.wc, aux.lam1, K0, 3);
-  gemmd(aux, GemmArgs<double>{aux.SlT, aux.wc, aux.wb, N, int(K2), K0, K0, K2, K2, 0, 0, 0}, 1, st);  // (z, ky, kx)
-  gemmd(aux, GemmArgs<double>{aux.SlT, aux.wb, aux.wa, N, K0, K0, K0, K0, K0, 0, K2, (long long)N * K0}, N,
-       st);                                                                                  // (z, y, kx)
-  gemmd(aux, GemmArgs<double>{aux.wa, aux.Sl, aux.zl, int(N2), N, K0, K0, N, N, 0, 0, 0}, 1, st);    // (z, y, x)
+  if (int rc = gemm(g4, 1, st)) return rc;
+  if (int rc = gemm(g5, N, st)) return rc;
+  return gemm(g6, 1, st);
 }
 
 // z = M^-1 r = S Lambda^-2 S r: the lowest modes in FP64, the rest in FP32.
-static void precond(const double *r, double *z, const ProbAux &aux, int N, int ndim, long long n,
-                    cudaStream_t st) {
+static int precond(const double *r, double *z, const ProbAux &aux, int N, int ndim, long long n,
+                   cudaStream_t st) {
   const int g = grid_for(n);
   const int K0 = pcg_low_modes(ndim, N);
-  precond_low(r, aux, N, K0, ndim, st);
+  if (int rc = precond_low(r, aux, N, K0, ndim, st)) return rc;
   k_to_f32<<<g, 256, 0, st>>>(r, aux.u0, n);
-  dst_all(aux.u0, aux.u1, aux.S, N, ndim, st);
-  k_inv_lambda2<<<g, 256, 0, st>>>(aux.u0, aux.lam1, N, ndim, n, K0);
-  dst_all(aux.u0, aux.u1, aux.S, N, ndim, st);
+  if (int rc = dst_all(aux.u0, aux.u1, aux.S, N, ndim, st)) return rc;
+  k_inv_lambda2<<<int(std::min<long long>(ndim == 3 ? (long long)N * N : N, 16LL * num_sms())), 256, 0, st>>>(
+      aux.u0, aux.lam1, N, ndim, K0);
+  if (int rc = dst_all(aux.u0, aux.u1, aux.S, N, ndim, st)) return rc;
   k_add_f32<<<g, 256, 0, st>>>(aux.u0, aux.zl, z, n);
+  return SC_OK;
 }
 
 // Dot products (u_k . v_k, k < nd) to the host.
@@ -521,7 +406,7 @@ int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t s
   // x0 = 0 (set by the plate set-up); each pass starts from the true residual
   for (int pass = 0; bn > 0 && pass < 8; ++pass) {
     resid(x, r);
-    precond(r, z, aux, N, nd, n, st);
+    if (int rc = precond(r, z, aux, N, nd, n, st)) return rc;
     cudaMemcpyAsync(p, z, size_t(n) * 8, cudaMemcpyDeviceToDevice, st);
     if (int rc = dots(r, z, r, r, nullptr, nullptr, 2, n, aux, st, hs)) return rc;
     double rz = hs[0], rn = std::sqrt(hs[1]);
@@ -542,7 +427,7 @@ int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t s
       }
       const double alpha = rz / pq;
       k_pcg_xr<<<g, 256, 0, st>>>(x, r, p, q, alpha, n);
-      precond(r, z, aux, N, nd, n, st);
+      if (int rc = precond(r, z, aux, N, nd, n, st)) return rc;
       if (int rc = dots(r, r, z, r, z, q, 3, n, aux, st, hs)) return rc;
       ++it;
       rn = std::sqrt(hs[0]);

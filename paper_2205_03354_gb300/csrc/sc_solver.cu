@@ -336,8 +336,6 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
     aux.wb = static_cast<double *>(cv.take(N * K0 * K0 * 8));
     aux.wc = static_cast<double *>(cv.take(K0 * K0 * K0 * 8));
     aux.zl = static_cast<double *>(cv.take(npts * 8));
-    aux.gp_cap = 16 * std::max<long long>((sp.ndim == 3 ? N * N : N) * K0, N * K0 * K0);
-    aux.gp = static_cast<double *>(cv.take(aux.gp_cap * 8));
   }
 }
 

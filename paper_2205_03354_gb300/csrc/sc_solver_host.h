@@ -37,8 +37,6 @@ struct ProbAux {
   // the lowest K0^ndim modes in FP64: their rows of the transform (K0 x N
   // and its transpose), transform work space and the FP64 result
   double *Sl = nullptr, *SlT = nullptr, *wa = nullptr, *wb = nullptr, *wc = nullptr, *zl = nullptr;
-  double *gp = nullptr;   // split-K partial sums of the FP64 products
-  long long gp_cap = 0;   // its length (doubles)
 };
 
 // Low-mode block edge of the preconditioner (modes with every index < K0
