@@ -184,14 +184,81 @@ __global__ void k_inv_lambda2(float *__restrict__ u, const double *__restrict__ 
   }
 }
 
-// x += a p, r -= a q
+// Scalars of the inner CG loop, kept on the device so that an iteration
+// needs no host round trip (and can be replayed from a CUDA graph).
+struct PcgScal {
+  double rz;       // z . r of the current direction
+  double alpha, beta;
+  double rn;       // ||r|| of the recurrence
+  double stop;     // the recurrence stops at rn <= stop
+  long long it, maxit;
+  int active;      // 0: converged, failed or out of iterations: kernels skip
+  int status;      // SC_OK, SC_ENOTCONV or SC_EBREAKDOWN
+};
+
+static_assert(sizeof(PcgScal) <= 24 * sizeof(double), "the scalars follow 8 result slots in a 32-double block");
+
+__global__ void k_pcg_scal_init(PcgScal *sc, double rz, double stop, long long it, long long maxit) {
+  sc->rz = rz;
+  sc->alpha = sc->beta = 0.0;
+  sc->rn = 0.0;
+  sc->stop = stop;
+  sc->it = it;
+  sc->maxit = maxit;
+  sc->active = 1;
+  sc->status = SC_OK;
+}
+// alpha = rz / (p . q)
+__global__ void k_pcg_alpha(PcgScal *sc, const double *__restrict__ out) {
+  if (!sc->active) return;
+  if (sc->it >= sc->maxit) {
+    sc->status = SC_ENOTCONV;
+    sc->active = 0;
+    return;
+  }
+  const double pq = out[0], rz = sc->rz;
+  if (!(pq > 0.0) || !(rz == rz)) {
+    sc->status = SC_EBREAKDOWN;
+    sc->active = 0;
+    return;
+  }
+  sc->alpha = rz / pq;
+}
+// out = {r.r, z.r, z.q}: the flexible direction update z_new . (r_new -
+// r_old) = -alpha z_new . q, and the recurrence's stopping test
+__global__ void k_pcg_beta(PcgScal *sc, const double *__restrict__ out) {
+  if (!sc->active) return;
+  ++sc->it;
+  const double rn = sqrt(out[0]);
+  sc->rn = rn;
+  if (!(rn == rn)) {
+    sc->status = SC_EBREAKDOWN;
+    sc->active = 0;
+    return;
+  }
+  sc->beta = -sc->alpha * out[2] / sc->rz;
+  sc->rz = out[1];
+  if (rn <= sc->stop) sc->active = 0;
+}
+// x += alpha p, r -= alpha q
 __global__ void k_pcg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                         const double *__restrict__ q, double a, long long n) {
+                         const double *__restrict__ q, const PcgScal *__restrict__ sc, long long n) {
+  if (!sc->active) return;
+  const double a = sc->alpha;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);
     r[i] = fma(-a, q[i], r[i]);
   }
+}
+// p = z + beta p
+__global__ void k_pcg_p(double *__restrict__ p, const double *__restrict__ z, const PcgScal *__restrict__ sc,
+                        long long n) {
+  if (!sc->active) return;
+  const double b = sc->beta;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(b, p[i], z[i]);
 }
 // r = b - A x for the plate operator (zero ghost ring) with the sum of the
 // products carried in double-double: each product w x is split exactly by
@@ -228,12 +295,6 @@ __global__ void k_resid_dd(const double *__restrict__ x, const double *__restric
 }
 
 // p = z + b p
-__global__ void k_pcg_p(double *__restrict__ p, const double *__restrict__ z, double b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    p[i] = fma(b, p[i], z[i]);
-}
-
 // Up to three dot products in one pass: part[k * nblk + blk] = sum over the
 // block's chunk of u_k . v_k (fixed order), then k_pcg_sum adds the parts.
 constexpr int PD_NTHR = 256, PD_CHUNK = PD_NTHR * 16;
@@ -351,7 +412,49 @@ static int dots(const double *u0, const double *v0, const double *u1, const doub
   return SC_OK;
 }
 
-int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st, double *res) {
+// A non-blocking stream per host thread and device for the solve (the
+// caller's stream may be the legacy default stream, which cannot be
+// captured into a graph), with the event that orders it after the caller's
+// earlier work.
+struct PcgStreams {
+  cudaStream_t s[64] = {};
+  cudaEvent_t e[64] = {};
+  ~PcgStreams() {
+    for (int i = 0; i < 64; ++i) {
+      if (e[i]) cudaEventDestroy(e[i]);
+      if (s[i]) cudaStreamDestroy(s[i]);
+    }
+  }
+};
+
+static int solve_stream(cudaStream_t caller, cudaStream_t *out) {
+  thread_local PcgStreams ps;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaStream_t &s = ps.s[dev & 63];
+  cudaEvent_t &e = ps.e[dev & 63];
+  if (!s && (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess))
+    return fail(SC_ECUDA, "preconditioned CG: stream creation failed");
+  cudaEventRecord(e, caller);
+  cudaStreamWaitEvent(s, e, 0);
+  *out = s;
+  return SC_OK;
+}
+
+static int pcg_on(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st, double *res);
+
+int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t caller, double *res) {
+  // the whole solve runs on the thread's own stream, and nothing of it is
+  // left in flight when this returns, on success or on error
+  cudaStream_t st = nullptr;
+  if (int rc = solve_stream(caller, &st)) return rc;
+  const int rc = pcg_on(sp, P, aux, st, res);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
+static int pcg_on(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t st, double *res) {
   const int N = int(sp.n[0]), nd = sp.ndim;
   const long long n = P.npts;
   const int g = grid_for(n);
@@ -397,6 +500,52 @@ int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t s
   }
   double *x = P.x, *b = P.rhs, *r = P.r, *p = static_cast<double *>(P.p), *q = static_cast<double *>(P.q),
          *z = aux.z;
+  PcgScal *dsc = reinterpret_cast<PcgScal *>(aux.out + 8);
+  const int nblk = int(pcg_parts(n));
+  auto dots_enq = [&](const double *u0, const double *v0, const double *u1, const double *v1, const double *u2,
+                      const double *v2, int ndot) {
+    k_pcg_dots<<<nblk, PD_NTHR, 0, st>>>(u0, v0, u1, v1, u2, v2, ndot, n, aux.part);
+    k_pcg_sum<<<1, PD_NTHR, 0, st>>>(aux.part, nblk, ndot, aux.out);
+  };
+  // One inner iteration, enqueued with no host synchronisation; once the
+  // recurrence has stopped, its own kernels return at once.
+  auto iteration = [&]() -> int {
+    if (int rc = apply(p, q)) return rc;
+    dots_enq(p, q, nullptr, nullptr, nullptr, nullptr, 1);
+    k_pcg_alpha<<<1, 1, 0, st>>>(dsc, aux.out);
+    k_pcg_xr<<<g, 256, 0, st>>>(x, r, p, q, dsc, n);
+    if (int rc = precond(r, z, aux, N, nd, n, st)) return rc;
+    dots_enq(r, r, z, r, z, q, 3);
+    k_pcg_beta<<<1, 1, 0, st>>>(dsc, aux.out);
+    k_pcg_p<<<g, 256, 0, st>>>(p, z, dsc, n);
+    return SC_OK;
+  };
+  // The iteration as a CUDA graph, captured after the first batch has run
+  // (so that every library set-up is done) and replayed from then on; a
+  // stream that cannot be captured keeps launching the iteration directly.
+  struct Exec {
+    cudaGraphExec_t e = nullptr;
+    ~Exec() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } graph;
+  bool tried = false;
+  auto try_capture = [&]() {
+    tried = true;
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const int rc = iteration();
+    const cudaError_t e = cudaStreamEndCapture(st, &gr);
+    if (rc == SC_OK && e == cudaSuccess && gr && cudaGraphInstantiate(&graph.e, gr, 0) != cudaSuccess)
+      graph.e = nullptr;
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    clear_error();
+  };
+  constexpr int BATCH = 4;  // iterations between reads of the scalars
   double hs[3];
   if (int rc = dots(b, b, nullptr, nullptr, nullptr, nullptr, 1, n, aux, st, hs)) return rc;
   const double bn = std::sqrt(hs[0]), tol = sp.rtol;
@@ -409,40 +558,31 @@ int run_pcg(const ProbSpec &sp, SolveProb &P, const ProbAux &aux, cudaStream_t s
     if (int rc = precond(r, z, aux, N, nd, n, st)) return rc;
     cudaMemcpyAsync(p, z, size_t(n) * 8, cudaMemcpyDeviceToDevice, st);
     if (int rc = dots(r, z, r, r, nullptr, nullptr, 2, n, aux, st, hs)) return rc;
-    double rz = hs[0], rn = std::sqrt(hs[1]);
+    const double rz = hs[0], rn = std::sqrt(hs[1]);
     rel = rn / bn;
     if (rel <= tol) break;  // the true residual meets the tolerance
-    bool conv = false;
-    while (!conv) {
-      if (it >= sp.maxit) {
-        status = SC_ENOTCONV;
+    // the recurrence is driven a little below the tolerance: on the largest
+    // grids the recomputed residual differs from it by rounding of the same
+    // order (the operator's weights scale as h^-4)
+    k_pcg_scal_init<<<1, 1, 0, st>>>(dsc, rz, 0.25 * tol * bn, it, sp.maxit);
+    for (;;) {
+      for (int k = 0; k < BATCH; ++k) {
+        if (graph.e) {
+          if (cudaGraphLaunch(graph.e, st) != cudaSuccess) return fail(SC_ECUDA, "preconditioned CG graph launch");
+        } else if (int rc = iteration()) {
+          return rc;
+        }
+      }
+      PcgScal hsc;
+      cudaMemcpyAsync(&hsc, dsc, sizeof(hsc), cudaMemcpyDeviceToHost, st);
+      const cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return fail(SC_ECUDA, "preconditioned CG: %s", cudaGetErrorString(e));
+      it = hsc.it;
+      if (!hsc.active) {
+        status = hsc.status;
         break;
       }
-      if (int rc = apply(p, q)) return rc;
-      double pq;
-      if (int rc = dots(p, q, nullptr, nullptr, nullptr, nullptr, 1, n, aux, st, &pq)) return rc;
-      if (!(pq > 0.0) || !(rz == rz)) {
-        status = SC_EBREAKDOWN;
-        break;
-      }
-      const double alpha = rz / pq;
-      k_pcg_xr<<<g, 256, 0, st>>>(x, r, p, q, alpha, n);
-      if (int rc = precond(r, z, aux, N, nd, n, st)) return rc;
-      if (int rc = dots(r, r, z, r, z, q, 3, n, aux, st, hs)) return rc;
-      ++it;
-      rn = std::sqrt(hs[0]);
-      if (!(rn == rn)) {
-        status = SC_EBREAKDOWN;
-        break;
-      }
-      // flexible direction update: z_new . (r_new - r_old) = -alpha z_new . q
-      const double beta = -alpha * hs[2] / rz;
-      rz = hs[1];
-      // the recurrence is driven a little below the tolerance: on the largest
-      // grids the recomputed residual differs from it by rounding of the
-      // same order (the operator's weights scale as h^-4)
-      conv = rn <= 0.25 * tol * bn;
-      if (!conv) k_pcg_p<<<g, 256, 0, st>>>(p, z, beta, n);
+      if (!tried) try_capture();
     }
     if (status != SC_OK) break;
   }

@@ -328,7 +328,7 @@ void layout(const ProbSpec &sp, Carver &cv, SolveProb &P, ProbAux &aux) {
     aux.S = static_cast<float *>(cv.take(N * N * 4));
     aux.lam1 = static_cast<double *>(cv.take(N * 8));
     aux.part = static_cast<double *>(cv.take(3 * pcg_parts(npts) * 8));
-    aux.out = static_cast<double *>(cv.take(8 * 8));
+    aux.out = static_cast<double *>(cv.take(32 * 8));  // dot results, then the inner loop's scalars
     const long long K0 = pcg_low_modes(sp.ndim, N);
     aux.Sl = static_cast<double *>(cv.take(K0 * N * 8));
     aux.SlT = static_cast<double *>(cv.take(K0 * N * 8));

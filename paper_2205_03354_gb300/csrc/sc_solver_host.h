@@ -33,7 +33,7 @@ struct ProbAux {
   float *u0 = nullptr, *u1 = nullptr;  // FP32 transform buffers
   float *S = nullptr;              // DST-I matrix, N x N
   double *lam1 = nullptr;          // 1D Dirichlet eigenvalues, N
-  double *part = nullptr, *out = nullptr;  // dot-product partials and results
+  double *part = nullptr, *out = nullptr;  // dot-product partials; results (8) and loop scalars
   // the lowest K0^ndim modes in FP64: their rows of the transform (K0 x N
   // and its transpose), transform work space and the FP64 result
   double *Sl = nullptr, *SlT = nullptr, *wa = nullptr, *wb = nullptr, *wc = nullptr, *zl = nullptr;
