@@ -321,7 +321,7 @@ def run_apply_e2e(sc, cases, dev, stream, args, world):
 
     for _ in range(max(1, args.warmup)):
         step()
-    nsteps = max(1, min(args.steps, 20))  # each e2e step moves ~4.8 GB over the host link
+    nsteps = max(1, min(args.steps, 60))  # each e2e step moves ~4.8 GB over the host link (~16 ms)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
