@@ -23,7 +23,11 @@
  *  - The library never calls cudaMalloc on a user path: every device buffer,
  *    including scratch ("work") space, is passed in by the caller, whose size
  *    is given by the matching *_work_bytes query.  The serving loop
- *    sub-allocates from a caller-provided device arena.
+ *    sub-allocates from a caller-provided device arena.  One exception: the
+ *    preconditioned solver (SC_SOLVER_PCG) runs its dense transform products
+ *    through cuBLAS, which allocates its own handle resources and GEMM work
+ *    space; the handle (and a non-blocking stream) is created on a thread's
+ *    first such solve on a device and kept until that thread exits.
  *  - Invalid arguments return SC_EINVAL before any device work is enqueued.
  *
  * The Python binding (paper_2205_03354_gb300) exposes each function under
@@ -285,11 +289,14 @@ typedef enum {
 typedef enum {
   SC_SOLVER_PERSISTENT = 0, /* one cooperative launch runs the whole CG loop  */
   SC_SOLVER_PLAIN = 1,      /* one kernel per CG operation, host-driven loop  */
-  SC_SOLVER_PCG = 2         /* plate problems only: host-driven FP64 CG
-                               preconditioned by the inverse of L_D^2 (L_D the
-                               Dirichlet Laplacian) applied with sine transforms
-                               in FP32; tens of iterations where plain CG needs
-                               O(N^2) (large grids)                              */
+  SC_SOLVER_PCG = 2         /* plate problems only: FP64 CG preconditioned by
+                               the inverse of L_D^2 (L_D the Dirichlet
+                               Laplacian) applied with sine transforms (cuBLAS
+                               GEMMs, FP32 accuracy; the lowest 16^d modes in
+                               FP64); tens of iterations where plain CG needs
+                               O(N^2) (large grids).  The loop's scalars stay on
+                               the device; an iteration is replayed from a CUDA
+                               graph on the calling thread's own stream        */
 } sc_solver_kind;
 
 typedef struct {
