@@ -429,6 +429,14 @@ int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_
     if (clash) cudaStreamWaitEvent(hp.in, hp.out_done[b], 0);
     cudaStreamWaitEvent(st, hp.out_done[b], 0);
   }
+  // an error after the first enqueue leaves nothing of this call in flight
+  auto drain = [&](int rc) {
+    cudaStreamSynchronize(hp.in);
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(hp.out);
+    hp.y_lo = hp.y_hi = 0;
+    return rc;
+  };
   std::vector<StageRun> runs;
   int last = 0;
   for (int k = 0; k < p.K; ++k) {
@@ -441,7 +449,7 @@ int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_
     if (!p.slabs) {
       const size_t xb = grid_elems_ext(p.nd, dims, bc == SC_BC_GHOSTED ? p.Rc : 0) * es;
       if (cudaMemcpyAsync(stg, xh, xb, cudaMemcpyHostToDevice, hp.in) != cudaSuccess)
-        return fail(SC_ECUDA, "host-to-device copy failed");
+        return drain(fail(SC_ECUDA, "host-to-device copy failed"));
     } else {
       stage_runs(p, k, z0, z1, runs);
       const size_t pb = size_t(p.pin) * es;
@@ -454,7 +462,7 @@ int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_
           e = cudaMemcpyAsync(stg + r.dst * pb, prev + r.src * pb, r.n * pb, cudaMemcpyDeviceToDevice, hp.in);
         else
           e = cudaMemsetAsync(stg + r.dst * pb, 0, r.n * pb, hp.in);
-        if (e != cudaSuccess) return fail(SC_ECUDA, "slab copy-in failed: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return drain(fail(SC_ECUDA, "slab copy-in failed: %s", cudaGetErrorString(e)));
       }
     }
     cudaEventRecord(hp.in_done[b], hp.in);
@@ -471,18 +479,18 @@ int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_
       sd[p.nd - 1] = nz;
       const void *xin = stg;
       if (bc != SC_BC_GHOSTED) {
-        if ((rc = ring_fill(p, dims, stg, w + p.off_pad[b], int(nz + 2 * p.Rc), st))) return rc;
+        if ((rc = ring_fill(p, dims, stg, w + p.off_pad[b], int(nz + 2 * p.Rc), st))) return drain(rc);
         xin = w + p.off_pad[b];
       }
       rc = run_choice(outer, inner, &C, dtype, SC_BC_GHOSTED, sd, h_num, h_den, xin, ys, w + p.off_work, c, st);
     }
-    if (rc) return rc;
+    if (rc) return drain(rc);
     cudaEventRecord(hp.comp_done[b], st);
     // copy-out
     cudaStreamWaitEvent(hp.out, hp.comp_done[b], 0);
     const size_t ob = size_t(nz) * p.pout * es;
     if (cudaMemcpyAsync(yh + size_t(z0) * p.pout * es, ys, ob, cudaMemcpyDeviceToHost, hp.out) != cudaSuccess)
-      return fail(SC_ECUDA, "device-to-host copy failed");
+      return drain(fail(SC_ECUDA, "device-to-host copy failed"));
     cudaEventRecord(hp.out_done[b], hp.out);
     hp.used[b] = true;
   }
@@ -491,7 +499,7 @@ int sc_apply_tuned_host(const sc_stencil *outer, const sc_stencil *inner, int32_
   hp.y_lo = reinterpret_cast<uintptr_t>(ybase);
   hp.y_hi = reinterpret_cast<uintptr_t>(ybase + p.ynum * p.ybytes);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(SC_ECUDA, "host apply: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return drain(fail(SC_ECUDA, "host apply: %s", cudaGetErrorString(e)));
   clear_error();
   return SC_OK;
 }
